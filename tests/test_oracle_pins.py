@@ -1,0 +1,399 @@
+"""Pins of the FP64 CPU oracle against facts fixed outside it: an independent
+Philox implementation, libm, closed forms, numerical integration of the ERDF
+density, numpy's FFT, Parseval, TK95 ensemble statistics and the invariants
+of the E13 iteration (Sec. 2.1, Sec. 3.2.2, App. A)."""
+import json
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_06374_gb300 import workloads
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+ERDF_BASE = np.array([-4.0, 0.0, -1.5, 0.4, -2.5])
+PSD_BASE = np.array([1.0 / 300.0, 1.0, 2.0])
+
+
+# ------------------------------------------------------------------ Philox
+_TRITON_SCRIPT = textwrap.dedent(r"""
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def k(c_ptr, out_ptr, seed, n: tl.constexpr):
+        i = tl.arange(0, n)
+        c0 = tl.load(c_ptr + 4 * i + 0); c1 = tl.load(c_ptr + 4 * i + 1)
+        c2 = tl.load(c_ptr + 4 * i + 2); c3 = tl.load(c_ptr + 4 * i + 3)
+        a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+        tl.store(out_ptr + 4 * i + 0, a); tl.store(out_ptr + 4 * i + 1, b)
+        tl.store(out_ptr + 4 * i + 2, c); tl.store(out_ptr + 4 * i + 3, d)
+
+    req = json.loads(sys.stdin.read())
+    res = []
+    for seed, ctrs in req:
+        c = torch.tensor(np.array(ctrs, dtype=np.uint32).view(np.int32))
+        o = torch.zeros_like(c)
+        k[(1,)](c, o, seed, c.numel() // 4)
+        res.append((o.numpy().view(np.uint32)).tolist())
+    print(json.dumps(res))
+""")
+
+
+def test_philox_matches_independent_implementation():
+    """Philox4x32-10 (Salmon et al. 2011) against Triton's CPU interpreter, an
+    implementation written independently of the oracle: random keys and counters."""
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    req = []
+    for s in range(6):
+        seed = int(rng.integers(0, 2**63)) if s else 0
+        ctrs = rng.integers(0, 2**32, size=(32, 4), dtype=np.uint64).astype(np.uint32)
+        if s == 0:
+            ctrs[0] = 0
+            ctrs[1] = 0xFFFFFFFF
+        req.append((seed, ctrs.reshape(-1).tolist()))
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    p = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(req),
+                       capture_output=True, text=True, env=env, timeout=600)
+    if p.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + p.stderr[-300:])
+    res = json.loads(p.stdout.strip().splitlines()[-1])
+    for (seed, ctrs), ref in zip(req, res):
+        ctr = np.array(ctrs, dtype=np.uint32).reshape(-1, 4)
+        key = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32), (ctr.shape[0], 1))
+        got = oracle.philox(ctr, key)
+        assert np.array_equal(got.reshape(-1), np.array(ref, dtype=np.uint32)), seed
+
+
+def test_philox_bits_are_uniform():
+    """Each of the 128 output bits is set about half the time over 2^14 counters."""
+    n = 1 << 14
+    ctr = np.zeros((n, 4), dtype=np.uint32); ctr[:, 0] = np.arange(n); ctr[:, 2] = 5
+    key = np.tile(np.array([1, 0], dtype=np.uint32), (n, 1))
+    out = oracle.philox(ctr, key)
+    bits = np.unpackbits(out.view(np.uint8), bitorder="little").reshape(n, 128)
+    frac = bits.mean(axis=0)
+    assert np.all(np.abs(frac - 0.5) < 5 * 0.5 / math.sqrt(n))
+
+
+def test_u01_closed_forms():
+    assert oracle.u01(0, 0) == 2.0 ** -53
+    assert oracle.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert oracle.u01(0, 0x80000000) == 0.5 + 2.0 ** -53
+    # bits below the top 52 of w1:w0 are dropped
+    assert oracle.u01(0xFFF, 0) == 2.0 ** -53
+
+
+# ------------------------------------------------------- bit-reproducible exp/log
+def _ulp_err(got, ref):
+    return np.abs(got - ref) / np.spacing(np.abs(ref))
+
+
+def test_spec_exp_within_2ulp_of_libm():
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-40, 10, 200000), rng.uniform(-1e-6, 1e-6, 1000),
+                        np.arange(-30, 8) * math.log(2)])
+    ref = np.array([math.exp(v) for v in x])
+    assert _ulp_err(oracle.spec_exp(x), ref).max() <= 2.0
+    assert oracle.spec_exp(0.0)[0] == 1.0
+    assert oracle.spec_exp(1.0)[0] == pytest.approx(math.e, rel=3e-16)
+
+
+def test_spec_log_within_2ulp_of_libm():
+    rng = np.random.default_rng(2)
+    x = np.concatenate([np.exp(rng.uniform(-40, 10, 200000)), 1 + rng.uniform(-1e-3, 1e-3, 2000),
+                        [0.5, 2.0, 1e-300, 1e300, math.sqrt(0.5), math.sqrt(2)]])
+    ref = np.array([math.log(v) for v in x])
+    got = oracle.spec_log(x)
+    assert _ulp_err(got, ref).max() <= 2.0
+    assert oracle.spec_log(1.0)[0] == 0.0
+    for k in range(-20, 21):
+        assert oracle.spec_log(2.0 ** k)[0] == pytest.approx(k * math.log(2), rel=2.3e-16, abs=0)
+
+
+def test_spec_log1p_within_2ulp_of_libm():
+    rng = np.random.default_rng(3)
+    y = np.concatenate([rng.uniform(-0.99, 20, 100000), rng.uniform(-1e-9, 1e-9, 1000),
+                        -np.exp(rng.uniform(-30, -0.01, 1000))])
+    ref = np.array([math.log1p(v) for v in y])
+    assert _ulp_err(oracle.spec_log1p(y), ref).max() <= 2.0
+    assert oracle.spec_log1p(1e-20)[0] == 1e-20
+
+
+# ---------------------------------------------------------------- ERDF draws
+def _density_logspace(u, erdf, linear_space=False):
+    """The ERDF density per unit log10(lambda), written from its definition: a
+    broken power law in lambda, continuous at the break.  In linear space the
+    slopes are per unit lambda, and dN/dlog10(lambda) = ln10 * lambda * dN/dlambda."""
+    umin, umax, ub, a1, a2 = erdf
+    lam, lamb = 10.0 ** u, 10.0 ** ub
+    if linear_space:
+        per_lam = np.where(u < ub, (lam / lamb) ** a1, (lam / lamb) ** a2)
+        return per_lam * lam * math.log(10)
+    return np.where(u < ub, (lam / lamb) ** a1, (lam / lamb) ** a2)
+
+
+def _cdf_table(erdf, linear_space=False, m=2_000_001):
+    u = np.linspace(erdf[0], erdf[1], m)
+    d = _density_logspace(u, erdf, linear_space)
+    c = np.concatenate([[0.0], np.cumsum((d[1:] + d[:-1]) * 0.5 * np.diff(u))])
+    return u, c / c[-1]
+
+
+@pytest.mark.parametrize("erdf,lin", [(ERDF_BASE, 0), (np.array([-4.0, 0.0, -0.7, 0.4, -1.6]), 0),
+                                      (np.array([-3.75, 0.5, -1.84, -0.47, -2.53]), 0),
+                                      (np.array([-4.0, 0.0, -1.5, 0.4, -2.5]), 1),
+                                      (np.array([-4.0, 0.0, -2.0, 0.0, -2.0]), 0)])
+def test_erdf_draws_follow_the_integrated_density(erdf, lin):
+    """KS distance of 2^17 oracle draws against the CDF obtained by numerically
+    integrating the density, and the sample mean against its integral."""
+    n = 1 << 17
+    x = oracle.erdf_draws(erdf, n, seed=11, curve_id=3, prec=1, linear_space=lin)
+    assert x.min() >= 10 ** erdf[0] * (1 - 1e-15) and x.max() <= 10 ** erdf[1] * (1 + 1e-15)
+    u_grid, cdf = _cdf_table(erdf, lin)
+    F = np.interp(np.log10(np.sort(x)), u_grid, cdf)
+    emp = np.arange(1, n + 1) / n
+    D = max(np.max(emp - F), np.max(F - (emp - 1.0 / n)))
+    assert D < 1.95 / math.sqrt(n)  # 0.1 % KS critical value
+    dens = _density_logspace(u_grid, erdf, lin)
+    lam = 10.0 ** u_grid
+    mean = np.trapezoid(lam * dens, u_grid) / np.trapezoid(dens, u_grid)
+    sd = math.sqrt(np.trapezoid(lam ** 2 * dens, u_grid) / np.trapezoid(dens, u_grid) - mean ** 2)
+    assert abs(x.mean() - mean) < 5 * sd / math.sqrt(n)
+
+
+def test_erdf_icdf_endpoints_and_break():
+    erdf = ERDF_BASE
+    lo = oracle.erdf_icdf(erdf, [2.0 ** -53])[0]
+    hi = oracle.erdf_icdf(erdf, [1.0 - 2.0 ** -53])[0]
+    # U = 1 - 2^-53 sits where the density is ~1.5e-4 of its peak, so the inverse
+    # is ill-conditioned there: 1e-16 in U moves log10(lambda) by ~1e-12.
+    assert lo == pytest.approx(1e-4, rel=1e-12) and hi == pytest.approx(1.0, rel=1e-10)
+    u_grid, cdf = _cdf_table(erdf)
+    Fb = float(np.interp(erdf[2], u_grid, cdf))
+    assert oracle.erdf_icdf(erdf, [Fb])[0] == pytest.approx(10 ** erdf[2], rel=1e-5)
+    U = np.linspace(1e-6, 1 - 1e-6, 10001)
+    assert np.all(np.diff(oracle.erdf_icdf(erdf, U)) >= 0)
+
+
+def test_erdf_float_rounding_is_round_to_nearest():
+    d64 = oracle.erdf_draws(ERDF_BASE, 4096, 5, 9, prec=1)
+    d32 = oracle.erdf_draws(ERDF_BASE, 4096, 5, 9, prec=0)
+    assert np.array_equal(d32, d64.astype(np.float32).astype(np.float64))
+
+
+def test_sharp_erdf_brackets_eq1_of_the_paper():
+    """The sharp broken power law with slopes -delta1 / -delta2 and break lambda*
+    lies within a factor 2 of Eq. 1's smooth form, at every lambda (paper
+    parameters from the golden fixture)."""
+    here = os.path.dirname(__file__)
+    with open(os.path.join(here, "golden", "paper_parameters.json")) as f:
+        g = json.load(f)
+    w = g["erdf_broken_power_law_eq1"]
+    u = np.linspace(-6, 2, 801)
+    lam_over = 10 ** (u - w["log_lambda_star"])
+    smooth = 1.0 / (lam_over ** w["delta1"] + lam_over ** w["delta2"])
+    erdf = np.array([-6.0, 2.0, w["log_lambda_star"], -w["delta1"], -w["delta2"]])
+    sharp = _density_logspace(u, erdf)
+    r = smooth / sharp
+    assert np.all(r <= 1.0 + 1e-12) and np.all(r >= 0.5 - 1e-12)
+    # and the oracle's draws for that parameter set follow the sharp density
+    x = oracle.erdf_draws(np.array([-3.75, 0.5, w["log_lambda_star"], -w["delta1"], -w["delta2"]]),
+                          1 << 15, 1, 0, prec=1)
+    assert x.min() >= 10 ** -3.75 * (1 - 1e-12) and x.max() <= 10 ** 0.5 * (1 + 1e-12)
+
+
+# ------------------------------------------------------------------- PSD
+def test_psd_eq3_shape():
+    f_br, a_lo, a_hi = 1 / 300.0, 1.0, 2.0
+    assert oracle.psd(f_br, f_br, a_lo, a_hi) == pytest.approx(0.5, rel=1e-15)
+    f1, f2 = 1e-9, 2e-9
+    lo_slope = math.log(oracle.psd(f2, f_br, a_lo, a_hi) / oracle.psd(f1, f_br, a_lo, a_hi)) / math.log(2)
+    f1, f2 = 1e3, 2e3
+    hi_slope = math.log(oracle.psd(f2, f_br, a_lo, a_hi) / oracle.psd(f1, f_br, a_lo, a_hi)) / math.log(2)
+    assert lo_slope == pytest.approx(-a_lo, abs=1e-5)
+    assert hi_slope == pytest.approx(-a_hi, abs=1e-5)
+
+
+# ------------------------------------------------------------------ DFT/FFT
+@pytest.mark.parametrize("n", [2, 4, 16, 64, 128, 1024, 4096])
+def test_fft_matches_numpy_and_direct_sum(n):
+    rng = np.random.default_rng(n)
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = np.fft.fft(z)
+    got = oracle.fft(z, -1)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    inv = oracle.fft(z, +1)
+    assert np.max(np.abs(inv - np.fft.ifft(z) * n)) <= 1e-12 * np.max(np.abs(ref))
+    if n <= 1024:
+        direct = oracle.dft(z, -1)
+        assert np.max(np.abs(got - direct)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_fft_parseval_and_closed_forms():
+    n = 2048
+    rng = np.random.default_rng(0)
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    Z = oracle.fft(z)
+    assert np.sum(np.abs(Z) ** 2) == pytest.approx(n * np.sum(np.abs(z) ** 2), rel=1e-12)
+    imp = np.zeros(n, complex); imp[0] = 1.0
+    assert np.allclose(oracle.fft(imp), 1.0, atol=1e-15)
+    k0 = 37
+    cosine = np.cos(2 * np.pi * k0 * np.arange(n) / n)
+    C = oracle.fft(cosine)
+    expect = np.zeros(n); expect[k0] = n / 2; expect[n - k0] = n / 2
+    assert np.max(np.abs(C - expect)) < 1e-10
+
+
+@pytest.mark.parametrize("n", [16, 64, 256, 4096])
+def test_real_transforms(n):
+    rng = np.random.default_rng(n + 1)
+    x = rng.standard_normal(n)
+    X = oracle.r2c(x)
+    assert np.max(np.abs(X - np.fft.rfft(x))) <= 1e-12 * np.max(np.abs(X))
+    assert abs(X[0].imag) < 1e-12 and abs(X[-1].imag) < 1e-12
+    Y = rng.standard_normal(n // 2 + 1) + 1j * rng.standard_normal(n // 2 + 1)
+    y = oracle.c2r(Y, n)
+    ref = np.fft.irfft(Y, n) * n
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # inverse of forward without normalisation is n times the identity
+    assert np.allclose(oracle.c2r(oracle.r2c(x), n), n * x, rtol=0, atol=1e-11 * n)
+
+
+# ---------------------------------------------------------------- TK95 stage
+def test_tk_spectrum_ensemble_matches_psd():
+    """E|X_j|^2 = P_j for 0<j<N/2 (complex Gaussian, TK95) and X_{N/2}^2 has mean
+    P_{N/2}: per-bin chi-square (2M dof) within 99.99 % bounds and the pooled
+    statistic within 5 sigma.  Frequencies f_j = j/(N dt) (App. A)."""
+    from scipy import stats
+    log2n, dt, M = 7, 3.0, 400
+    n = 1 << log2n
+    psd = np.array([0.01, 1.0, 2.5])
+    f = np.arange(n // 2 + 1) / (n * dt)
+    P = np.array([0.0] + [oracle.psd(v, *psd) for v in f[1:]])
+    Xs = np.array([oracle.tk_spectrum(log2n, dt, psd, 17, c) for c in range(M)])
+    assert np.all(Xs[:, 0] == 0) and np.all(Xs[:, -1].imag == 0)
+    chi = np.sum(np.abs(Xs[:, 1:-1]) ** 2, axis=0) / (P[1:-1] / 2)  # ~ chi2(2M)
+    lo, hi = stats.chi2.ppf([5e-5, 1 - 5e-5], 2 * M)
+    assert np.all((chi > lo) & (chi < hi))
+    pooled = chi.sum(); dof = 2 * M * chi.size
+    assert abs(pooled - dof) < 5 * math.sqrt(2 * dof)
+    nyq = np.sum(Xs[:, -1].real ** 2) / P[-1]
+    lo1, hi1 = stats.chi2.ppf([5e-5, 1 - 5e-5], M)
+    assert lo1 < nyq < hi1
+
+
+def test_tk_series_normalisation_and_amplitudes():
+    log2n = 12; n = 1 << log2n
+    x, A, sigma = oracle.tk_series(log2n, 1.0, PSD_BASE, 1, 0)
+    assert abs(x.mean()) < 1e-14 and abs(x.std() - 1.0) < 1e-13
+    X = oracle.tk_spectrum(log2n, 1.0, PSD_BASE, 1, 0)
+    assert A[0] == 0.0
+    assert np.allclose(A[1:] * sigma, np.abs(X[1:]), rtol=1e-14, atol=0)
+    # the series is the inverse transform of X: its forward transform returns N X / sigma
+    Xr = np.fft.rfft(x)
+    assert np.allclose(Xr[1:], n * X[1:] / sigma, rtol=0, atol=1e-9 * np.abs(Xr).max())
+    # against numpy's inverse real FFT of the same spectrum
+    ref = np.fft.irfft(X, n) * n
+    ref = (ref - ref.mean()) / ref.std()
+    assert np.max(np.abs(x - ref)) < 1e-12
+
+
+# --------------------------------------------------------------- E13 iteration
+def _tk_state(log2n, seed=1, psd=PSD_BASE):
+    x, A, _ = oracle.tk_series(log2n, 1.0, psd, seed, 0)
+    return x, A
+
+
+def test_iteration_fixed_point():
+    """With draws equal to the TK series values and the state equal to the TK
+    series, one iteration reproduces the TK series bit for bit (amplitudes and
+    phases already agree, so the ranks do not change)."""
+    x, A = _tk_state(10)
+    s = np.sort(x)
+    out, _, _ = oracle.iterate(A, s, x, 1)
+    assert np.array_equal(out, x)
+
+
+def test_iteration_scale_and_dc_invariance():
+    log2n = 11
+    n = 1 << log2n
+    _, A = _tk_state(log2n, 3)
+    d = oracle.erdf_draws(ERDF_BASE, n, 3, 0, prec=1)
+    s = np.sort(d)
+    a, _, _ = oracle.iterate(A, s, d, 3)
+    A2 = A * 3.7
+    A2[0] = 5.0
+    b, _, _ = oracle.iterate(A2, s, d, 3)
+    assert np.array_equal(a, b)
+
+
+def test_iteration_is_a_permutation_and_rank_consistent():
+    log2n = 12
+    n = 1 << log2n
+    _, A = _tk_state(log2n, 4)
+    d = oracle.erdf_draws(ERDF_BASE, n, 4, 0, prec=0)
+    s = np.sort(d)
+    out, xa, perm = oracle.iterate(A, s, d, 5, want_adj=True)
+    assert np.array_equal(np.sort(out), s)
+    order = np.argsort(xa, kind="stable")
+    assert np.array_equal(order, perm)
+    assert np.all(np.diff(out[order]) >= 0)
+
+
+def test_iteration_brute_force_small():
+    """N = 16 against a direct transcription with numpy's FFT and stable argsort."""
+    n = 16
+    rng = np.random.default_rng(5)
+    A = np.abs(rng.standard_normal(n // 2 + 1)); A[0] = 0.0
+    s = np.sort(rng.uniform(0, 1, n))
+    x0 = rng.permutation(s)
+    X = np.fft.rfft(x0)
+    Y = A * X / np.abs(X)
+    Y[0] = A[0]
+    Y[-1] = A[-1] * (1.0 if X[-1].real >= 0 else -1.0)
+    xa = np.fft.irfft(Y, n) * n
+    expect = np.empty(n); expect[np.argsort(xa, kind="stable")] = s
+    got, _, _ = oracle.iterate(A, s, x0, 1)
+    assert np.array_equal(got, expect)
+
+
+def test_generate_output_is_the_draw_multiset():
+    j = workloads.job(12, 20, seed=9, curve_id=4)
+    r = oracle.generate(j, prec=0, want=("x", "s", "tk", "A"))
+    draws = oracle.erdf_draws(ERDF_BASE, 1 << 12, 9, 4, prec=0)
+    assert np.array_equal(np.sort(r["x"]), np.sort(draws))
+    assert np.array_equal(r["s"], np.sort(draws))
+
+
+def test_generate_periodogram_follows_psd_shape():
+    """Averaged over curves, the periodogram of the final series falls with
+    frequency like the input PSD (Sec. 3.2.4, 'Periodogram'): log-log correlation."""
+    log2n = 12; n = 1 << log2n
+    jobs = [workloads.job(log2n, 30, seed=c, curve_id=c, f_br=1 / 100.0) for c in range(8)]
+    x, _ = oracle.generate_batch(jobs, prec=0, nthreads=4)
+    x = x.reshape(8, n)
+    per = np.mean(np.abs(np.fft.rfft(x - x.mean(axis=1, keepdims=True), axis=1)) ** 2, axis=0)[1:]
+    f = np.arange(1, n // 2 + 1) / n
+    P = np.array([oracle.psd(v, 1 / 100.0, 1.0, 2.0) for v in f])
+    edges = np.unique(np.logspace(0, math.log10(n // 2), 20).astype(int))
+    lp = [np.log(per[a - 1:b - 1].mean()) for a, b in zip(edges[:-1], edges[1:])]
+    lP = [np.log(P[a - 1:b - 1].mean()) for a, b in zip(edges[:-1], edges[1:])]
+    assert np.corrcoef(lp, lP)[0, 1] > 0.95
+
+
+def test_batch_equals_single():
+    jobs = [workloads.job(10, 3, seed=c, curve_id=c) for c in range(5)]
+    x, used = oracle.generate_batch(jobs, prec=0, nthreads=3)
+    assert used == 3
+    single = np.concatenate([oracle.generate(j, prec=0)["x"] for j in jobs])
+    assert np.array_equal(x, single)
