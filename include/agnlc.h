@@ -1,0 +1,205 @@
+/*
+ * agnlc.h -- C ABI of the GB300 light-curve generator.
+ *
+ * The library generates batches of AGN Eddington-ratio light curves with a
+ * prescribed power spectral density (bending power law, Sec. 2.1.2, Eq. 3) and
+ * a prescribed probability density (the Eddington-ratio distribution function,
+ * ERDF, Sec. 2.1.1) by the method of Sec. 2.1 of Sartori et al. (2019):
+ *   1. a Timmer & Koenig (TK95) Gaussian realisation of the PSD;
+ *   2. a random draw of N values from the ERDF (here by inverse CDF);
+ *   3. iterative amplitude adjustment (Schreiber & Schmitz 1996 /
+ *      Emmanoulopoulos et al. 2013, Sec. 3.2.2): forward FFT, target
+ *      amplitudes with the phases kept, inverse FFT, rank-order replacement by
+ *      the sorted draws.
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types only; no exceptions cross the boundary; every call returns
+ *     an lc_status (0 = LC_OK, negative = error).  Arguments are validated
+ *     before any device work is queued; an invalid call changes nothing.
+ *   - "device pointer" means memory of the plan's CUDA device (cudaMalloc,
+ *     torch, ...); "host pointer" means ordinary or pinned host memory.
+ *   - The caller owns every output buffer.  The library owns its plans and
+ *     servers and the device workspaces they allocate.
+ *   - Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ *     default stream).  Calls are asynchronous with respect to the host
+ *     unless stated otherwise; work is ordered after everything queued on the
+ *     stream before the call, and later work on that stream sees the results.
+ *   - A series of N = 2^log2n samples is stored contiguously, sample k at time
+ *     t_k = k * dt.  A batch is the concatenation of its curves in job order
+ *     (curve c starts at sum_{c' < c} N_{c'}).  Element type: float for
+ *     LC_FP32, double for LC_FP64.
+ *   - Results are deterministic functions of (job, precision): the same job
+ *     gives the same bits alone, in any batch, and in the server.
+ */
+#ifndef AGNLC_H
+#define AGNLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LC_API __attribute__((visibility("default")))
+#else
+#define LC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LC_OK = 0,
+    LC_PENDING = 1,             /* lc_poll: the job has not finished yet          */
+    LC_ERR_INVALID = -1,        /* an argument or job parameter is out of range   */
+    LC_ERR_NOMEM = -2,          /* a device or host allocation failed             */
+    LC_ERR_CUDA = -3,           /* a CUDA call failed (message: lc_last_error)    */
+    LC_ERR_TIMEOUT = -4,        /* a bounded device wait gave up                  */
+    LC_ERR_BUSY = -5,           /* lc_submit: the admission queue is full         */
+    LC_ERR_UNKNOWN_TICKET = -6  /* lc_poll: no such ticket (or already collected)  */
+} lc_status;
+
+typedef enum { LC_FP32 = 0, LC_FP64 = 1 } lc_precision;
+
+/* PSD of Eq. 3 with A = 1: P(f) = [(f/f_br)^alpha_low + (f/f_br)^alpha_high]^-1.
+ * f_br is in inverse units of dt (e.g. day^-1 when dt is in days); the PSD
+ * falls as f^-alpha_low below and f^-alpha_high above the break. */
+typedef struct {
+    double f_br;
+    double alpha_low;
+    double alpha_high;
+} lc_psd;
+
+/* ERDF: a broken power law in u = log10(lambda) on [log_lmin, log_lmax] with a
+ * sharp break at log_lbreak (the sharp-break form of Eq. 1):
+ * dN/dlog10(lambda) ~ lambda^slope_low below and lambda^slope_high above the
+ * break.  linear_space != 0 states the slopes for dN/dlambda instead (the
+ * linear sampling of Sec. 2.1.1), i.e. both are raised by one in log space. */
+typedef struct {
+    double log_lmin;
+    double log_lmax;
+    double log_lbreak;
+    double slope_low;
+    double slope_high;
+    int32_t linear_space;
+} lc_erdf;
+
+/* One light curve (the inputs of Sec. 3.2.4: t_bin = dt, N_steps = 2^log2n).
+ * seed and curve_id key the counter-based random streams; two jobs with the
+ * same (seed, curve_id) draw the same random numbers. */
+typedef struct {
+    uint32_t log2n;      /* 4 <= log2n <= 27 (N up to 2^27, Sec. 3.2.3)         */
+    uint32_t iters;      /* number of amplitude-adjustment iterations, >= 0     */
+    double dt;           /* sampling interval, > 0                              */
+    lc_psd psd;
+    lc_erdf erdf;
+    uint64_t seed;
+    uint64_t curve_id;
+} lc_job;
+
+typedef struct lc_plan_s* lc_plan;
+typedef struct lc_server_s* lc_server;
+typedef uint64_t lc_ticket;
+
+/* Human-readable name of a status code (static storage). */
+LC_API const char* lc_status_string(lc_status status);
+
+/* Text of the most recent error raised on the calling thread (static per
+ * thread; empty string if none). */
+LC_API const char* lc_last_error(void);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Validate `njobs` jobs and build a plan for them on CUDA device `device`:
+ * the ragged layout, twiddle tables and every device workspace the batch
+ * needs (allocated here, owned by the plan).  jobs: host array, read only
+ * during the call.  Validation: njobs >= 1, 4 <= log2n <= 27, dt > 0,
+ * f_br > 0, finite slopes, log_lmin < log_lbreak < log_lmax; otherwise
+ * LC_ERR_INVALID.  LC_ERR_NOMEM if the workspace does not fit.  Blocking. */
+LC_API lc_status lc_plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device,
+                         lc_plan* out);
+
+/* Device bytes the plan holds (workspace + tables). */
+LC_API lc_status lc_plan_workspace_bytes(lc_plan plan, size_t* bytes);
+
+/* Total samples sum_c N_c of the batch (the length of out_x). */
+LC_API lc_status lc_plan_total_samples(lc_plan plan, size_t* samples);
+
+/* The whole generator (Sec. 2.1): TK95 realisation, ERDF draws, then each
+ * job's `iters` iterations.  out_x: device pointer, sum_c N_c elements, the
+ * final series.  out_tk: device pointer or NULL; when given it receives the
+ * normalised TK95 series (zero mean, unit variance) of every curve. */
+LC_API lc_status lc_generate(lc_plan plan, void* out_x, void* out_tk, void* stream);
+
+/* As lc_generate, but out_x / out_tk are HOST pointers (pinned memory is
+ * fastest); the device-to-host copies are part of the call, which returns
+ * after they have completed (blocking). */
+LC_API lc_status lc_generate_host(lc_plan plan, void* out_x_host, void* out_tk_host, void* stream);
+
+/* Setup only (steps 1-2 of Sec. 2.1): computes the target amplitudes, the
+ * sorted draws and the initial state (the draws in draw order) inside the
+ * plan; out_tk as in lc_generate. */
+LC_API lc_status lc_setup(lc_plan plan, void* out_tk, void* stream);
+
+/* Run amplitude-adjustment iterations (Sec. 3.2.2) on the plan's current
+ * state.  iters = 0 runs each job's own count; iters > 0 runs exactly that
+ * many on every curve.  Requires a previous lc_setup or lc_generate. */
+LC_API lc_status lc_iterate(lc_plan plan, uint32_t iters, void* stream);
+
+/* Copy the plan's current state (sum_c N_c elements) to / from a device
+ * buffer.  lc_set_state lets a caller iterate from a state of its own; the
+ * values must then be a permutation of each curve's draws for the output to
+ * keep the ERDF exactly. */
+LC_API lc_status lc_get_state(lc_plan plan, void* out_x, void* stream);
+LC_API lc_status lc_set_state(lc_plan plan, const void* in_x, void* stream);
+
+/* Read-only view of a plan buffer, valid until lc_plan_destroy:
+ * which = 0: state x (sum N elements); 1: target amplitudes A
+ * (sum (N/2+1) elements, curve c at sum_{c'<c} (N_{c'}/2+1)); 2: sorted
+ * draws s (sum N elements). */
+LC_API lc_status lc_plan_buffer(lc_plan plan, int which, const void** device_ptr, size_t* bytes);
+
+/* Number of kernel launches the most recent lc_generate/lc_iterate queued
+ * (graph replays count their kernels). */
+LC_API lc_status lc_plan_last_launches(lc_plan plan, uint64_t* launches);
+
+/* Device time of the last lc_generate / lc_generate_host / lc_setup +
+ * lc_iterate, split into the setup stage and the iteration stage, measured
+ * with CUDA events on the plan's stream (blocks until both are known).
+ * A stage that did not run reports 0. */
+LC_API lc_status lc_plan_timing(lc_plan plan, float* setup_ms, float* iterate_ms);
+
+/* Release the plan and its device memory (synchronises its stream). */
+LC_API lc_status lc_plan_destroy(lc_plan plan);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A continuous-batching server on `device`: jobs submitted at any time are
+ * admitted while their device footprint fits in hbm_budget_bytes, run in
+ * batched iteration steps alongside the other active jobs, and retired when
+ * their iteration count is reached.  A host thread owned by the server drives
+ * the device.  hbm_budget_bytes = 0 uses 80 % of the free device memory. */
+LC_API lc_status lc_server_create(int device, size_t hbm_budget_bytes, lc_precision prec,
+                           lc_server* out);
+
+/* Queue one job (copied; non-blocking).  LC_ERR_BUSY if the queue is full,
+ * LC_ERR_INVALID for a bad job. */
+LC_API lc_status lc_submit(lc_server server, const lc_job* job, lc_ticket* out);
+
+/* Non-blocking completion check.  LC_PENDING while the job runs; LC_OK when
+ * it has finished, after copying its N results into out (host pointer) and
+ * the submit-to-finish latency into *latency_ns (either may be NULL); the
+ * ticket is then released.  LC_ERR_UNKNOWN_TICKET otherwise. */
+LC_API lc_status lc_poll(lc_server server, lc_ticket ticket, void* out_host, uint64_t* latency_ns);
+
+/* Jobs finished, jobs active on the device, jobs waiting for admission. */
+LC_API lc_status lc_server_stats(lc_server server, uint64_t* finished, uint64_t* active,
+                          uint64_t* waiting);
+
+/* Stop the server thread, drop unfinished jobs and free its memory. */
+LC_API lc_status lc_server_destroy(lc_server server);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AGNLC_H */

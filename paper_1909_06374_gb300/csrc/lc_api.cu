@@ -1,0 +1,571 @@
+// lc_api.cu -- plans and the batch entry points of the C ABI (agnlc.h).
+//
+// A plan lays a batch of curves out in flat ragged buffers (curve c at
+// sum_{c'<c} N_{c'}), groups curves of equal length into classes, and owns one
+// device arena holding the state, the target amplitudes, the sorted draws, the
+// FFT and sort scratch and the twiddle tables.  lc_setup runs the TK95 and
+// ERDF stages (Sec. 2.1, steps one and two); lc_iterate replays one captured
+// CUDA graph per amplitude-adjustment iteration (Sec. 3.2.2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "lc_internal.h"
+
+namespace lc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error_text() { return g_last_error.c_str(); }
+
+#define LC_CK(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+            return LC_ERR_CUDA;                                                              \
+        }                                                                                    \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+__global__ void k_iter_increment(int* d_iter) { ++*d_iter; }
+
+__global__ void k_eff_iters(const CurveDev* __restrict__ curves, int n, uint32_t override_iters,
+                            uint32_t* __restrict__ eff, int* __restrict__ d_iter)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) eff[c] = override_iters ? override_iters : curves[c].iters;
+    if (c == 0) *d_iter = 0;
+}
+
+__global__ void k_iter_add(int* d_iter, uint32_t n) { *d_iter += (int)n; }
+
+void launch_iter_increment(const Plan& p, cudaStream_t st) { k_iter_increment<<<1, 1, 0, st>>>(p.d_iter); }
+void launch_iter_add(const Plan& p, uint32_t n, cudaStream_t st) { k_iter_add<<<1, 1, 0, st>>>(p.d_iter, n); }
+
+void launch_eff_iters(const Plan& p, uint32_t override_iters, cudaStream_t st)
+{
+    k_eff_iters<<<(int)((p.ncurves + 255) / 256), 256, 0, st>>>(p.d_curves, (int)p.ncurves, override_iters,
+                                                                p.d_eff_iters, p.d_iter);
+}
+
+static bool finite(double v) { return std::isfinite(v); }
+
+lc_status validate_job(const lc_job& j)
+{
+    if (j.log2n < 4 || j.log2n > 27) { set_error("log2n must be in [4, 27]"); return LC_ERR_INVALID; }
+    if (!(j.dt > 0) || !finite(j.dt)) { set_error("dt must be > 0"); return LC_ERR_INVALID; }
+    if (!(j.psd.f_br > 0) || !finite(j.psd.f_br)) { set_error("f_br must be > 0"); return LC_ERR_INVALID; }
+    if (!finite(j.psd.alpha_low) || !finite(j.psd.alpha_high)) { set_error("PSD slopes must be finite"); return LC_ERR_INVALID; }
+    const lc_erdf& e = j.erdf;
+    if (!finite(e.log_lmin) || !finite(e.log_lmax) || !finite(e.log_lbreak) || !finite(e.slope_low) ||
+        !finite(e.slope_high)) { set_error("ERDF parameters must be finite"); return LC_ERR_INVALID; }
+    if (!(e.log_lmin < e.log_lbreak && e.log_lbreak < e.log_lmax)) {
+        set_error("ERDF needs log_lmin < log_lbreak < log_lmax"); return LC_ERR_INVALID;
+    }
+    if (e.log_lmin < -300 || e.log_lmax > 300) { set_error("ERDF range out of [1e-300, 1e300]"); return LC_ERR_INVALID; }
+    if (std::fabs(e.slope_low) > 50 || std::fabs(e.slope_high) > 50) { set_error("ERDF slope magnitude > 50"); return LC_ERR_INVALID; }
+    return LC_OK;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename T>
+static lc_status build_tables(Plan& p)
+{
+    for (auto& k : p.classes) launch_twiddles<T>(k, p.stream);
+    LC_CK(cudaGetLastError());
+    return LC_OK;
+}
+
+lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device, Plan** out)
+{
+    if (!jobs || njobs == 0 || !out) { set_error("null jobs / out or njobs == 0"); return LC_ERR_INVALID; }
+    if (prec != LC_FP32 && prec != LC_FP64) { set_error("bad precision"); return LC_ERR_INVALID; }
+    for (size_t i = 0; i < njobs; ++i) {
+        lc_status s = validate_job(jobs[i]);
+        if (s != LC_OK) { set_error("job " + std::to_string(i) + ": " + g_last_error); return s; }
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("no such CUDA device"); return LC_ERR_INVALID;
+    }
+    DeviceGuard g(device);
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) return LC_ERR_NOMEM;
+    p->device = device;
+    p->prec = prec;
+    p->ncurves = njobs;
+    p->jobs.assign(jobs, jobs + njobs);
+    const size_t ts = prec == LC_FP32 ? 4 : 8;
+
+    // curves in job order; classes by length
+    p->h_curves.resize(njobs);
+    size_t off = 0, offh = 0;
+    std::vector<int> cls_of_len(28, -1);
+    for (size_t c = 0; c < njobs; ++c) {
+        const lc_job& j = jobs[c];
+        CurveDev& cv = p->h_curves[c];
+        cv.off = off; cv.offh = offh; cv.log2n = j.log2n; cv.iters = j.iters;
+        cv.dt = j.dt; cv.f_br = j.psd.f_br; cv.a_lo = j.psd.alpha_low; cv.a_hi = j.psd.alpha_high;
+        cv.umin = j.erdf.log_lmin; cv.umax = j.erdf.log_lmax; cv.ub = j.erdf.log_lbreak;
+        cv.sl_lo = j.erdf.slope_low; cv.sl_hi = j.erdf.slope_high; cv.lin = j.erdf.linear_space ? 1 : 0;
+        cv.seed = j.seed; cv.curve_id = j.curve_id;
+        if (cls_of_len[j.log2n] < 0) {
+            cls_of_len[j.log2n] = (int)p->classes.size();
+            p->classes.emplace_back();
+            p->classes.back().log2n = j.log2n;
+        }
+        cv.cls = cls_of_len[j.log2n];
+        p->classes[cv.cls].h_curves.push_back((int)c);
+        off += 1ull << j.log2n;
+        offh += (1ull << (j.log2n - 1)) + 1;
+        p->max_iters = std::max(p->max_iters, j.iters);
+    }
+    p->total = off;
+    p->total_h = offh;
+
+    // arena layout
+    size_t hist = 0, cbase = 0, partial = 0, twb = 0;
+    for (auto& k : p->classes) {
+        k.ncurves = (int)k.h_curves.size();
+        k.radices = fft_radices(k.log2n - 1);
+        const size_t n = 1ull << k.log2n;
+        k.tile_len = (int)std::min<size_t>(n, kSortTile);
+        k.tiles_per_curve = (int)(n / k.tile_len);
+        k.nchunks = (k.tiles_per_curve + kScanChunk - 1) / kScanChunk;
+        k.hist_off = hist;  hist += (size_t)k.ncurves * k.tiles_per_curve * 256;
+        k.cbase_off = cbase; cbase += (size_t)k.ncurves * k.nchunks * 256;
+        k.partial_off = partial; partial += (size_t)k.ncurves * spec_blocks_per_curve(k.log2n);
+        twb += align_up((n / 2) * 2 * ts, 256);
+    }
+    const size_t A256 = 256;
+    size_t sz = 0;
+    auto take = [&](size_t bytes) { size_t o = sz; sz = align_up(sz + bytes, A256); return o; };
+    const size_t o_curves = take(sizeof(CurveDev) * njobs);
+    const size_t o_erdf = take(sizeof(ErdfConst) * njobs);
+    const size_t o_sigma = take(sizeof(double) * njobs);
+    const size_t o_eff = take(sizeof(uint32_t) * njobs);
+    const size_t o_iter = take(sizeof(int) * 4);
+    const size_t o_partial = take(sizeof(double) * partial);
+    const size_t o_x = take(p->total * ts);
+    const size_t o_f = take(p->total * ts);
+    const size_t o_A = take(p->total_h * ts);
+    const size_t o_s = take(p->total * ts);
+    const size_t sortbytes = std::max(2 * p->total * ts + 2 * p->total * 4, 16 * p->total_h);
+    const size_t o_sort = take(sortbytes);
+    const size_t o_hist = take(sizeof(uint32_t) * hist);
+    const size_t o_cbase = take(sizeof(uint32_t) * cbase);
+    const size_t o_tw = take(twb);
+    const size_t o_cls = take(sizeof(int) * njobs);
+    p->arena_bytes = sz;
+    if (cudaMalloc(&p->arena, sz) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of " + std::to_string(sz) + " bytes failed");
+        delete p;
+        return LC_ERR_NOMEM;
+    }
+    char* base = (char*)p->arena;
+    p->d_curves = (CurveDev*)(base + o_curves);
+    p->d_erdf = (ErdfConst*)(base + o_erdf);
+    p->d_sigma = (double*)(base + o_sigma);
+    p->d_eff_iters = (uint32_t*)(base + o_eff);
+    p->d_iter = (int*)(base + o_iter);
+    p->d_partial = (double*)(base + o_partial);
+    p->d_x = base + o_x;
+    p->d_f = base + o_f;
+    p->d_A = base + o_A;
+    p->d_s = base + o_s;
+    p->d_keysA = base + o_sort;
+    p->d_keysB = base + o_sort + p->total * ts;
+    p->d_valsA = (uint32_t*)(base + o_sort + 2 * p->total * ts);
+    p->d_valsB = (uint32_t*)(base + o_sort + 2 * p->total * ts + p->total * 4);
+    p->d_spec = (double2*)(base + o_sort);
+    p->d_hist = (uint32_t*)(base + o_hist);
+    p->d_cbase = (uint32_t*)(base + o_cbase);
+    size_t tw_at = o_tw, cls_at = o_cls;
+    for (auto& k : p->classes) {
+        k.d_tw = base + tw_at;
+        tw_at += align_up((((size_t)1 << k.log2n) / 2) * 2 * ts, 256);
+        k.d_curves = (int*)(base + cls_at);
+        cls_at += sizeof(int) * k.h_curves.size();
+    }
+    p->tw_bytes = twb;
+
+    auto fail = [&](const char* what, cudaError_t e) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        cudaFree(p->arena);
+        delete p;
+        return LC_ERR_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail("stream", e);
+    cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming);
+    cudaEventCreate(&p->t_setup0);
+    cudaEventCreate(&p->t_setup1);
+    cudaEventCreate(&p->t_it0);
+    cudaEventCreate(&p->t_it1);
+    if ((e = cudaMemcpyAsync(p->d_curves, p->h_curves.data(), sizeof(CurveDev) * njobs, cudaMemcpyHostToDevice,
+                             p->stream)) != cudaSuccess) return fail("upload curves", e);
+    for (auto& k : p->classes) {
+        if ((e = cudaMemcpyAsync(k.d_curves, k.h_curves.data(), sizeof(int) * k.h_curves.size(),
+                                 cudaMemcpyHostToDevice, p->stream)) != cudaSuccess) return fail("upload classes", e);
+    }
+    lc_status st = prec == LC_FP32 ? build_tables<float>(*p) : build_tables<double>(*p);
+    if (st != LC_OK) { cudaFree(p->arena); delete p; return st; }
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail("plan sync", e);
+    for (auto& k : p->classes) k.resident = resident_supported(*p, k.log2n);
+    *out = p;
+    return LC_OK;
+}
+
+// ------------------------------------------------------------ stages
+template <typename T>
+static lc_status run_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* launches)
+{
+    cudaEventRecord(p.t_setup0, st);
+    p.timed_setup = true;
+    p.timed_iter = false;
+    launch_eff_iters(p, 0, st);
+    ++*launches;
+    for (auto& k : p.classes) { launch_tk_spectrum(p, k, st); *launches += 2; }
+    for (auto& k : p.classes) { launch_amplitudes<T>(p, k, st); ++*launches; }
+    if (out_tk) {
+        for (auto& k : p.classes) {
+            launch_spectral_tk<T>(p, k, p.d_f, st);
+            ++*launches;
+            launch_fft<T>(p, k, true, p.d_f, p.d_x, out_tk, false, st, launches);
+        }
+    }
+    launch_erdf_constants(p, st);
+    ++*launches;
+    for (auto& k : p.classes) { launch_erdf_draws<T>(p, k, st); ++*launches; }
+    for (auto& k : p.classes) launch_sort<T>(p, k, p.d_x, kSortKeysToValues, false, st, launches);
+    cudaEventRecord(p.t_setup1, st);
+    LC_CK(cudaGetLastError());
+    p.setup_done = true;
+    return LC_OK;
+}
+
+// One amplitude-adjustment iteration of every class (Sec. 3.2.2).
+template <typename T>
+static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches)
+{
+    for (auto& k : p.classes) {
+        if (k.resident) continue;
+        void* R1 = launch_fft<T>(p, k, false, p.d_x, p.d_f, nullptr, true, st, launches);
+        void* Zp = (R1 == p.d_x) ? p.d_f : p.d_x;
+        launch_spectral_iter<T>(p, k, R1, Zp, st);
+        ++*launches;
+        void* R3 = launch_fft<T>(p, k, true, Zp, R1, nullptr, true, st, launches);
+        launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches);
+    }
+    launch_iter_increment(p, st);
+    ++*launches;
+}
+
+// Runs `n_it` more iterations.  reset: start from iteration 0 with every
+// curve's budget = override_iters (or its job count); otherwise continue
+// from the plan's current iteration index with the budgets already set.
+template <typename T>
+static lc_status run_iterations_impl(Plan& p, uint32_t override_iters, uint32_t n_it, bool reset,
+                                     cudaStream_t st, uint64_t* launches)
+{
+    if (!p.setup_done) { set_error("lc_iterate before lc_setup/lc_generate"); return LC_ERR_INVALID; }
+    cudaEventRecord(p.t_it0, st);
+    if (reset) {
+        launch_eff_iters(p, override_iters, st);
+        ++*launches;
+    }
+    // curves of the fused on-chip classes run all n_it iterations in one launch
+    for (auto& k : p.classes)
+        if (k.resident && n_it > 0) launch_resident(p, k, n_it, st, launches);
+    bool any_multi = false;
+    for (auto& k : p.classes) any_multi |= !k.resident;
+    if (any_multi && n_it > 0) {
+        if (!p.iter_graph) {
+            cudaGraph_t g = nullptr;
+            uint64_t per = 0;
+            LC_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            enqueue_iteration<T>(p, st, &per);
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (e != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(e)); return LC_ERR_CUDA; }
+            e = cudaGraphInstantiate(&p.iter_graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)); return LC_ERR_CUDA; }
+            p.launches_per_iter = per;
+        }
+        for (uint32_t it = 0; it < n_it; ++it) LC_CK(cudaGraphLaunch(p.iter_graph, st));
+        *launches += (uint64_t)n_it * p.launches_per_iter;
+    } else if (n_it > 0) {
+        launch_iter_add(p, n_it, st);
+        ++*launches;
+    }
+    cudaEventRecord(p.t_it1, st);
+    p.timed_iter = true;
+    LC_CK(cudaGetLastError());
+    return LC_OK;
+}
+
+template <typename T>
+static lc_status run_iterations(Plan& p, uint32_t override_iters, cudaStream_t st, uint64_t* launches)
+{
+    const uint32_t n_it = override_iters ? override_iters : p.max_iters;
+    return run_iterations_impl<T>(p, override_iters, n_it, true, st, launches);
+}
+
+lc_status plan_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* launches)
+{
+    return p.prec == LC_FP32 ? run_setup<float>(p, out_tk, st, launches) : run_setup<double>(p, out_tk, st, launches);
+}
+
+lc_status plan_continue(Plan& p, uint32_t n_it, cudaStream_t st, uint64_t* launches)
+{
+    return p.prec == LC_FP32 ? run_iterations_impl<float>(p, 0, n_it, false, st, launches)
+                             : run_iterations_impl<double>(p, 0, n_it, false, st, launches);
+}
+
+void plan_free(Plan* p)
+{
+    if (!p) return;
+    {
+        DeviceGuard g(p->device);
+        cudaStreamSynchronize(p->stream);
+        if (p->iter_graph) cudaGraphExecDestroy(p->iter_graph);
+        cudaFree(p->arena);
+        if (p->d_tk_stage) cudaFree(p->d_tk_stage);
+        cudaEventDestroy(p->ev_in);
+        cudaEventDestroy(p->ev_out);
+        cudaEventDestroy(p->t_setup0);
+        cudaEventDestroy(p->t_setup1);
+        cudaEventDestroy(p->t_it0);
+        cudaEventDestroy(p->t_it1);
+        cudaStreamDestroy(p->stream);
+    }
+    delete p;
+}
+
+struct StreamJoin {
+    Plan& p;
+    cudaStream_t user;
+    StreamJoin(Plan& pl, void* s) : p(pl), user((cudaStream_t)s)
+    {
+        cudaEventRecord(p.ev_in, user);
+        cudaStreamWaitEvent(p.stream, p.ev_in, 0);
+    }
+    ~StreamJoin()
+    {
+        cudaEventRecord(p.ev_out, p.stream);
+        cudaStreamWaitEvent(user, p.ev_out, 0);
+    }
+};
+
+}  // namespace lc
+
+using namespace lc;
+
+struct lc_plan_s : public lc::Plan {};
+
+extern "C" {
+
+const char* lc_status_string(lc_status s)
+{
+    switch (s) {
+    case LC_OK: return "LC_OK";
+    case LC_PENDING: return "LC_PENDING";
+    case LC_ERR_INVALID: return "LC_ERR_INVALID";
+    case LC_ERR_NOMEM: return "LC_ERR_NOMEM";
+    case LC_ERR_CUDA: return "LC_ERR_CUDA";
+    case LC_ERR_TIMEOUT: return "LC_ERR_TIMEOUT";
+    case LC_ERR_BUSY: return "LC_ERR_BUSY";
+    case LC_ERR_UNKNOWN_TICKET: return "LC_ERR_UNKNOWN_TICKET";
+    }
+    return "LC_UNKNOWN_STATUS";
+}
+
+const char* lc_last_error(void) { return g_last_error.c_str(); }
+
+lc_status lc_plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device, lc_plan* out)
+{
+    if (!out) { set_error("out is null"); return LC_ERR_INVALID; }
+    Plan* p = nullptr;
+    lc_status s = plan_create(jobs, njobs, prec, device, &p);
+    if (s != LC_OK) return s;
+    *out = static_cast<lc_plan>(p);
+    return LC_OK;
+}
+
+lc_status lc_plan_workspace_bytes(lc_plan plan, size_t* bytes)
+{
+    if (!plan || !bytes) { set_error("null argument"); return LC_ERR_INVALID; }
+    *bytes = plan->arena_bytes;
+    return LC_OK;
+}
+
+lc_status lc_plan_total_samples(lc_plan plan, size_t* samples)
+{
+    if (!plan || !samples) { set_error("null argument"); return LC_ERR_INVALID; }
+    *samples = plan->total;
+    return LC_OK;
+}
+
+lc_status lc_setup(lc_plan plan, void* out_tk, void* stream)
+{
+    if (!plan) { set_error("null plan"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    StreamJoin j(*plan, stream);
+    uint64_t n = 0;
+    lc_status s = plan->prec == LC_FP32 ? run_setup<float>(*plan, out_tk, plan->stream, &n)
+                                        : run_setup<double>(*plan, out_tk, plan->stream, &n);
+    plan->last_launches = n;
+    return s;
+}
+
+lc_status lc_iterate(lc_plan plan, uint32_t iters, void* stream)
+{
+    if (!plan) { set_error("null plan"); return LC_ERR_INVALID; }
+    if (!plan->setup_done) { set_error("lc_iterate before lc_setup/lc_generate"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    StreamJoin j(*plan, stream);
+    uint64_t n = 0;
+    lc_status s = plan->prec == LC_FP32 ? run_iterations<float>(*plan, iters, plan->stream, &n)
+                                        : run_iterations<double>(*plan, iters, plan->stream, &n);
+    plan->last_launches = n;
+    return s;
+}
+
+lc_status lc_generate(lc_plan plan, void* out_x, void* out_tk, void* stream)
+{
+    if (!plan || !out_x) { set_error("null plan or out_x"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    StreamJoin j(*plan, stream);
+    uint64_t n = 0;
+    lc_status s = plan->prec == LC_FP32 ? run_setup<float>(*plan, out_tk, plan->stream, &n)
+                                        : run_setup<double>(*plan, out_tk, plan->stream, &n);
+    if (s == LC_OK)
+        s = plan->prec == LC_FP32 ? run_iterations<float>(*plan, 0, plan->stream, &n)
+                                  : run_iterations<double>(*plan, 0, plan->stream, &n);
+    if (s == LC_OK) {
+        const size_t ts = plan->prec == LC_FP32 ? 4 : 8;
+        LC_CK(cudaMemcpyAsync(out_x, plan->d_x, plan->total * ts, cudaMemcpyDeviceToDevice, plan->stream));
+    }
+    plan->last_launches = n;
+    return s;
+}
+
+lc_status lc_generate_host(lc_plan plan, void* out_x_host, void* out_tk_host, void* stream)
+{
+    if (!plan || !out_x_host) { set_error("null plan or out_x_host"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    const size_t ts = plan->prec == LC_FP32 ? 4 : 8;
+    if (out_tk_host && !plan->d_tk_stage) {
+        if (cudaMalloc(&plan->d_tk_stage, plan->total * ts) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation of the TK95 staging buffer failed");
+            return LC_ERR_NOMEM;
+        }
+    }
+    uint64_t n = 0;
+    lc_status s;
+    {
+        StreamJoin j(*plan, stream);
+        void* tk = out_tk_host ? plan->d_tk_stage : nullptr;
+        s = plan->prec == LC_FP32 ? run_setup<float>(*plan, tk, plan->stream, &n)
+                                  : run_setup<double>(*plan, tk, plan->stream, &n);
+        if (s == LC_OK && out_tk_host)
+            LC_CK(cudaMemcpyAsync(out_tk_host, tk, plan->total * ts, cudaMemcpyDeviceToHost, plan->stream));
+        if (s == LC_OK)
+            s = plan->prec == LC_FP32 ? run_iterations<float>(*plan, 0, plan->stream, &n)
+                                      : run_iterations<double>(*plan, 0, plan->stream, &n);
+        if (s == LC_OK)
+            LC_CK(cudaMemcpyAsync(out_x_host, plan->d_x, plan->total * ts, cudaMemcpyDeviceToHost, plan->stream));
+    }
+    plan->last_launches = n;
+    if (s != LC_OK) return s;
+    LC_CK(cudaStreamSynchronize(plan->stream));
+    return LC_OK;
+}
+
+lc_status lc_get_state(lc_plan plan, void* out_x, void* stream)
+{
+    if (!plan || !out_x) { set_error("null argument"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    StreamJoin j(*plan, stream);
+    const size_t ts = plan->prec == LC_FP32 ? 4 : 8;
+    LC_CK(cudaMemcpyAsync(out_x, plan->d_x, plan->total * ts, cudaMemcpyDeviceToDevice, plan->stream));
+    return LC_OK;
+}
+
+lc_status lc_set_state(lc_plan plan, const void* in_x, void* stream)
+{
+    if (!plan || !in_x) { set_error("null argument"); return LC_ERR_INVALID; }
+    if (!plan->setup_done) { set_error("lc_set_state before lc_setup/lc_generate"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    StreamJoin j(*plan, stream);
+    const size_t ts = plan->prec == LC_FP32 ? 4 : 8;
+    LC_CK(cudaMemcpyAsync(plan->d_x, in_x, plan->total * ts, cudaMemcpyDeviceToDevice, plan->stream));
+    return LC_OK;
+}
+
+lc_status lc_plan_buffer(lc_plan plan, int which, const void** device_ptr, size_t* bytes)
+{
+    if (!plan || !device_ptr) { set_error("null argument"); return LC_ERR_INVALID; }
+    const size_t ts = plan->prec == LC_FP32 ? 4 : 8;
+    switch (which) {
+    case 0: *device_ptr = plan->d_x; if (bytes) *bytes = plan->total * ts; return LC_OK;
+    case 1: *device_ptr = plan->d_A; if (bytes) *bytes = plan->total_h * ts; return LC_OK;
+    case 2: *device_ptr = plan->d_s; if (bytes) *bytes = plan->total * ts; return LC_OK;
+    default: set_error("which must be 0, 1 or 2"); return LC_ERR_INVALID;
+    }
+}
+
+lc_status lc_plan_last_launches(lc_plan plan, uint64_t* launches)
+{
+    if (!plan || !launches) { set_error("null argument"); return LC_ERR_INVALID; }
+    *launches = plan->last_launches;
+    return LC_OK;
+}
+
+lc_status lc_plan_timing(lc_plan plan, float* setup_ms, float* iterate_ms)
+{
+    if (!plan) { set_error("null plan"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    float a = 0.f, b = 0.f;
+    if (plan->timed_setup) {
+        LC_CK(cudaEventSynchronize(plan->t_setup1));
+        LC_CK(cudaEventElapsedTime(&a, plan->t_setup0, plan->t_setup1));
+    }
+    if (plan->timed_iter) {
+        LC_CK(cudaEventSynchronize(plan->t_it1));
+        LC_CK(cudaEventElapsedTime(&b, plan->t_it0, plan->t_it1));
+    }
+    if (setup_ms) *setup_ms = a;
+    if (iterate_ms) *iterate_ms = b;
+    return LC_OK;
+}
+
+lc_status lc_plan_destroy(lc_plan plan)
+{
+    if (!plan) { set_error("null plan"); return LC_ERR_INVALID; }
+    plan_free(static_cast<Plan*>(plan));
+    return LC_OK;
+}
+
+}  // extern "C"

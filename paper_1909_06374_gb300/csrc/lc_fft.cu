@@ -1,0 +1,404 @@
+// lc_fft.cu -- batched Stockham FFT passes and the fused spectral step of one
+// amplitude-adjustment iteration (Sec. 2.1 third step; Sec. 3.2.2).
+//
+// A real series of N = 2M samples is transformed as the complex series
+// z[n] = x[2n] + i x[2n+1] of length M (the float array reinterpreted), so the
+// forward transform reads the state in place and the inverse transform writes
+// the real series directly.  The spectral kernel unpacks the half-length
+// spectrum into X_0..X_M, imposes the target amplitudes keeping the phases,
+// and packs the result for the inverse transform, all in one pass over the
+// conjugate pairs (k, M-k).
+#include "lc_internal.h"
+
+namespace lc {
+
+// ---------------------------------------------------------- constants
+__device__ __forceinline__ double cos16(int t)
+{
+    switch (t & 15) {
+    case 0: return 1.0;
+    case 1: return 0.92387953251128675613;
+    case 2: return 0.70710678118654752440;
+    case 3: return 0.38268343236508977173;
+    case 4: return 0.0;
+    case 5: return -0.38268343236508977173;
+    case 6: return -0.70710678118654752440;
+    case 7: return -0.92387953251128675613;
+    case 8: return -1.0;
+    case 9: return -0.92387953251128675613;
+    case 10: return -0.70710678118654752440;
+    case 11: return -0.38268343236508977173;
+    case 12: return 0.0;
+    case 13: return 0.38268343236508977173;
+    case 14: return 0.70710678118654752440;
+    default: return 0.92387953251128675613;
+    }
+}
+
+// b * e^{sign 2 pi i t/16}, sign = +1 for the inverse transform.
+template <typename T, bool INV>
+__device__ __forceinline__ cplx<T> rot16(cplx<T> b, int t)
+{
+    cplx<T> r;
+    if (t == 0) return b;
+    if (t == 4) {  // multiply by -i (forward) or +i (inverse)
+        if (INV) { r.x = -b.y; r.y = b.x; } else { r.x = b.y; r.y = -b.x; }
+        return r;
+    }
+    if (t == 8) { r.x = -b.x; r.y = -b.y; return r; }
+    const T c = (T)cos16(t);
+    const T s = INV ? (T)cos16(t + 12) : -(T)cos16(t + 12);  // sin(2 pi t/16) = cos(2 pi (t-4)/16)
+    r.x = b.x * c - b.y * s;
+    r.y = b.x * s + b.y * c;
+    return r;
+}
+
+__host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r >> 1); }
+__host__ __device__ constexpr int bitrev_c(int v, int bits)
+{
+    return bits == 0 ? 0 : (((v & 1) << (bits - 1)) | bitrev_c(v >> 1, bits - 1));
+}
+
+// In-register DFT of R <= 16 points: out[q] = sum_r u[r] e^{-+ 2 pi i r q/R}
+// (radix-2 decimation in time on bit-reversed input).
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_regs(cplx<T> (&u)[R])
+{
+    constexpr int LR = ilog2c(R);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int j = bitrev_c(i, LR);
+        if (j > i) { cplx<T> t = u[i]; u[i] = u[j]; u[j] = t; }
+    }
+#pragma unroll
+    for (int s = 1; s <= LR; ++s) {
+        const int m = 1 << s, h = m >> 1;
+#pragma unroll
+        for (int g = 0; g < R; g += m) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const cplx<T> a = u[g + j];
+                const cplx<T> b = rot16<T, INV>(u[g + j + h], j * (16 / m));
+                u[g + j] = cadd(a, b);
+                u[g + j + h] = csub(a, b);
+            }
+        }
+    }
+}
+
+// W_M^t = e^{-2 pi i t/M} from the class table rt[k] = e^{-2 pi i k/N} (N = 2M).
+template <typename T>
+__device__ __forceinline__ cplx<T> twiddle_M(const cplx<T>* __restrict__ rt, uint64_t t, uint64_t M)
+{
+    if (2 * t < M) return rt[2 * t];
+    cplx<T> w = rt[2 * t - M];
+    w.x = -w.x; w.y = -w.y;
+    return w;
+}
+
+// Table e^{-2 pi i k/N}, k < N/2, computed in FP64 and rounded once to T.
+template <typename T>
+__global__ void k_twiddles(cplx<T>* __restrict__ rt, uint32_t log2n)
+{
+    const uint64_t M = 1ull << (log2n - 1);
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-(double)k / (double)M, &s, &c);
+        cplx<T> w; w.x = (T)c; w.y = (T)s;
+        rt[k] = w;
+    }
+}
+
+struct PassArgs {
+    const int* cls_curves;
+    const CurveDev* curves;
+    const uint32_t* eff_iters;
+    const int* d_iter;   // null: every curve active
+    const void* tw;
+    const void* in;
+    void* out;
+    int ncurves;
+    uint32_t log2M;
+    uint32_t log2p;
+};
+
+// One radix-R Stockham pass (decimation in time, natural-order output) over
+// every curve of a class: with span p, butterfly i (k = i mod p) reads
+// u_r = z[i + r M/R], applies W_{Rp}^{rk}, takes an R-point DFT and writes
+// y[(i-k)R + k + r p].
+template <typename T, int R, bool INV>
+__global__ void __launch_bounds__(256) k_fft_pass(const PassArgs a)
+{
+    using V = cplx<T>;
+    constexpr int LR = ilog2c(R);
+    const uint32_t log2nb = a.log2M - LR;
+    const uint64_t nb = 1ull << log2nb;
+    const uint64_t total = (uint64_t)a.ncurves << log2nb;
+    const uint64_t p = 1ull << a.log2p;
+    const uint64_t M = 1ull << a.log2M;
+    const int it = a.d_iter ? *a.d_iter : 0;
+    const V* __restrict__ rt = (const V*)a.tw;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(t >> log2nb);
+        const uint64_t i = t & (nb - 1);
+        const int c = a.cls_curves[ci];
+        if (a.d_iter && (uint32_t)it >= a.eff_iters[c]) continue;
+        const uint64_t base = a.curves[c].off >> 1;
+        const V* __restrict__ src = (const V*)a.in + base;
+        V* __restrict__ dst = (V*)a.out + base;
+        V u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = src[i + (uint64_t)r * nb];
+        const uint64_t k = i & (p - 1);
+        if (p > 1) {
+            const uint64_t step = k << (a.log2M - LR - a.log2p);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                V w = twiddle_M<T>(rt, (uint64_t)r * step, M);
+                if (INV) w.y = -w.y;
+                u[r] = cmul(u[r], w);
+            }
+        }
+        dft_regs<T, R, INV>(u);
+        const uint64_t j = ((i - k) << LR) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[j + (uint64_t)r * p] = u[r];
+    }
+}
+
+// Phase kept, amplitude replaced: A X/|X|, and A (phase 0) when X = 0.
+__device__ __forceinline__ float2 keep_phase(float2 X, float A)
+{
+    const float m2 = X.x * X.x + X.y * X.y;
+    if (m2 == 0.0f) return make_float2(A, 0.0f);
+    const float s = A * rsqrtf(m2);
+    return make_float2(X.x * s, X.y * s);
+}
+__device__ __forceinline__ double2 keep_phase(double2 X, double A)
+{
+    const double m2 = X.x * X.x + X.y * X.y;
+    if (m2 == 0.0) return make_double2(A, 0.0);
+    const double s = A / sqrt(m2);
+    return make_double2(X.x * s, X.y * s);
+}
+
+// Pack Y_k, Y_{M-k} (a Hermitian half spectrum) for the length-M inverse
+// transform: Z'_k = E' + i O' with E' = Y_k + conj(Y_{M-k}),
+// O' = (Y_k - conj(Y_{M-k})) e^{+2 pi i k/N}; Z'_{M-k} = conj(E') + i conj(O').
+template <typename V>
+__device__ __forceinline__ void pack_pair(V Yk, V Ym, V W, V& Zk, V& Zm)
+{
+    const V Ep = cadd(Yk, cconj(Ym));
+    const V Op = cmul(csub(Yk, cconj(Ym)), cconj(W));
+    Zk.x = Ep.x - Op.y; Zk.y = Ep.y + Op.x;
+    Zm.x = Ep.x + Op.y; Zm.y = -Ep.y + Op.x;
+}
+
+struct SpecArgs {
+    const int* cls_curves;
+    const CurveDev* curves;
+    const uint32_t* eff_iters;
+    const int* d_iter;
+    const void* tw;
+    const void* Z;       // forward output (iteration) -- unused for TK
+    void* Zp;            // packed spectrum for the inverse transform
+    const void* A;
+    const double2* spec; // TK: FP64 spectrum
+    const double* sigma;
+    int ncurves;
+    uint32_t log2M;
+};
+
+// Iteration spectral step (E13): X from the packed forward transform
+// (X_k = E_k + W^k O_k with E_k = (Z_k + conj Z_{M-k})/2,
+// O_k = (Z_k - conj Z_{M-k})/(2i)), Y = keep_phase(X, A) with
+// Y_0 = A_0 and Y_M = A_M sign(X_M), then packed for the inverse.
+template <typename T>
+__global__ void __launch_bounds__(256) k_spectral_iter(const SpecArgs a)
+{
+    using V = cplx<T>;
+    const uint32_t log2h = a.log2M - 1;
+    const uint64_t half = 1ull << log2h;
+    const uint64_t M = 1ull << a.log2M;
+    const uint64_t total = (uint64_t)a.ncurves << log2h;
+    const int it = *a.d_iter;
+    const V* __restrict__ rt = (const V*)a.tw;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(t >> log2h);
+        const uint64_t k = t & (half - 1);
+        const int c = a.cls_curves[ci];
+        if ((uint32_t)it >= a.eff_iters[c]) continue;
+        const CurveDev& cv = a.curves[c];
+        const V* __restrict__ Z = (const V*)a.Z + (cv.off >> 1);
+        V* __restrict__ Zo = (V*)a.Zp + (cv.off >> 1);
+        const T* __restrict__ A = (const T*)a.A + cv.offh;
+        if (k == 0) {
+            const V z0 = Z[0];
+            const T XM = z0.x - z0.y;
+            const T Y0 = A[0];
+            const T YM = XM < (T)0 ? -A[M] : A[M];
+            V o; o.x = Y0 + YM; o.y = Y0 - YM;
+            Zo[0] = o;
+            // self-paired bin k = M/2: X = conj(Z), packed value 2 conj(Y)
+            const V Yh = keep_phase(cconj(Z[half]), A[half]);
+            V oh; oh.x = (T)2 * Yh.x; oh.y = -(T)2 * Yh.y;
+            Zo[half] = oh;
+        } else {
+            const V za = Z[k], zb = Z[M - k];
+            const V W = rt[k];
+            V E; E.x = (T)0.5 * (za.x + zb.x); E.y = (T)0.5 * (za.y - zb.y);
+            V O; O.x = (T)0.5 * (za.y + zb.y); O.y = (T)-0.5 * (za.x - zb.x);
+            const V WO = cmul(W, O);
+            const V Xk = cadd(E, WO);
+            const V Xm = cconj(csub(E, WO));
+            const V Yk = keep_phase(Xk, A[k]);
+            const V Ym = keep_phase(Xm, A[M - k]);
+            V Zk, Zm;
+            pack_pair(Yk, Ym, W, Zk, Zm);
+            Zo[k] = Zk;
+            Zo[M - k] = Zm;
+        }
+    }
+}
+
+// TK95 output: Y_j = X_j / sigma (FP64, rounded to T) packed for the inverse
+// transform, so that the transform yields the normalised TK95 series.
+template <typename T>
+__global__ void __launch_bounds__(256) k_spectral_tk(const SpecArgs a)
+{
+    using V = cplx<T>;
+    const uint32_t log2h = a.log2M - 1;
+    const uint64_t half = 1ull << log2h;
+    const uint64_t M = 1ull << a.log2M;
+    const uint64_t total = (uint64_t)a.ncurves << log2h;
+    const V* __restrict__ rt = (const V*)a.tw;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(t >> log2h);
+        const uint64_t k = t & (half - 1);
+        const int c = a.cls_curves[ci];
+        const CurveDev& cv = a.curves[c];
+        const double2* __restrict__ X = a.spec + cv.offh;
+        const double inv = 1.0 / a.sigma[c];
+        V* __restrict__ Zo = (V*)a.Zp + (cv.off >> 1);
+        if (k == 0) {
+            const T Y0 = (T)(X[0].x * inv), YM = (T)(X[M].x * inv);
+            V o; o.x = Y0 + YM; o.y = Y0 - YM;
+            Zo[0] = o;
+            V oh; oh.x = (T)2 * (T)(X[half].x * inv); oh.y = -(T)2 * (T)(X[half].y * inv);
+            Zo[half] = oh;
+        } else {
+            V Yk; Yk.x = (T)(X[k].x * inv); Yk.y = (T)(X[k].y * inv);
+            V Ym; Ym.x = (T)(X[M - k].x * inv); Ym.y = (T)(X[M - k].y * inv);
+            V Zk, Zm;
+            pack_pair(Yk, Ym, rt[k], Zk, Zm);
+            Zo[k] = Zk;
+            Zo[M - k] = Zm;
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+static int grid_for(uint64_t work, int block)
+{
+    uint64_t g = (work + block - 1) / block;
+    const uint64_t cap = 152ull * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+std::vector<int> fft_radices(uint32_t log2m)
+{
+    std::vector<int> r;
+    int rem = (int)(log2m % 4);
+    if (rem) r.push_back(1 << rem);
+    for (uint32_t q = 0; q < log2m / 4; ++q) r.push_back(16);
+    return r;
+}
+
+template <typename T>
+void launch_twiddles(const ClassInfo& k, cudaStream_t st)
+{
+    const uint64_t M = 1ull << (k.log2n - 1);
+    k_twiddles<T><<<grid_for(M, 256), 256, 0, st>>>((cplx<T>*)k.d_tw, k.log2n);
+}
+
+template <typename T, bool INV>
+static void launch_pass(int R, const PassArgs& a, uint64_t work, cudaStream_t st)
+{
+    const int g = grid_for(work, 256);
+    switch (R) {
+    case 2: k_fft_pass<T, 2, INV><<<g, 256, 0, st>>>(a); break;
+    case 4: k_fft_pass<T, 4, INV><<<g, 256, 0, st>>>(a); break;
+    case 8: k_fft_pass<T, 8, INV><<<g, 256, 0, st>>>(a); break;
+    default: k_fft_pass<T, 16, INV><<<g, 256, 0, st>>>(a); break;
+    }
+}
+
+template <typename T>
+void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void* other, void* final_out,
+                 bool gated, cudaStream_t st, uint64_t* launches)
+{
+    PassArgs a;
+    a.cls_curves = k.d_curves;
+    a.curves = p.d_curves;
+    a.eff_iters = p.d_eff_iters;
+    a.d_iter = gated ? p.d_iter : nullptr;
+    a.tw = k.d_tw;
+    a.ncurves = k.ncurves;
+    a.log2M = k.log2n - 1;
+    uint32_t log2p = 0;
+    void* cur = in;
+    void* nxt = other;
+    const size_t P = k.radices.size();
+    for (size_t q = 0; q < P; ++q) {
+        const int R = k.radices[q];
+        a.in = cur;
+        a.out = (q + 1 == P && final_out) ? final_out : nxt;
+        a.log2p = log2p;
+        const uint64_t work = (uint64_t)k.ncurves << (a.log2M - ilog2c(R));
+        if (inverse) launch_pass<T, true>(R, a, work, st);
+        else launch_pass<T, false>(R, a, work, st);
+        if (launches) ++*launches;
+        log2p += (uint32_t)ilog2c(R);
+        void* written = a.out;
+        nxt = cur;
+        cur = written;
+    }
+    return cur;
+}
+
+template <typename T>
+void launch_spectral_iter(const Plan& p, const ClassInfo& k, const void* Z, void* Zp, cudaStream_t st)
+{
+    SpecArgs a{};
+    a.cls_curves = k.d_curves; a.curves = p.d_curves; a.eff_iters = p.d_eff_iters; a.d_iter = p.d_iter;
+    a.tw = k.d_tw; a.Z = Z; a.Zp = Zp; a.A = p.d_A; a.ncurves = k.ncurves; a.log2M = k.log2n - 1;
+    const uint64_t work = (uint64_t)k.ncurves << (k.log2n - 2);
+    k_spectral_iter<T><<<grid_for(work, 256), 256, 0, st>>>(a);
+}
+
+template <typename T>
+void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_t st)
+{
+    SpecArgs a{};
+    a.cls_curves = k.d_curves; a.curves = p.d_curves; a.tw = k.d_tw; a.Zp = Zp; a.spec = p.d_spec;
+    a.sigma = p.d_sigma; a.ncurves = k.ncurves; a.log2M = k.log2n - 1;
+    const uint64_t work = (uint64_t)k.ncurves << (k.log2n - 2);
+    k_spectral_tk<T><<<grid_for(work, 256), 256, 0, st>>>(a);
+}
+
+template void launch_twiddles<float>(const ClassInfo&, cudaStream_t);
+template void launch_twiddles<double>(const ClassInfo&, cudaStream_t);
+template void* launch_fft<float>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*);
+template void* launch_fft<double>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*);
+template void launch_spectral_iter<float>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
+template void launch_spectral_iter<double>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
+template void launch_spectral_tk<float>(const Plan&, const ClassInfo&, void*, cudaStream_t);
+template void launch_spectral_tk<double>(const Plan&, const ClassInfo&, void*, cudaStream_t);
+
+}  // namespace lc

@@ -1,0 +1,132 @@
+// lc_internal.h -- host-side plan of the GB300 light-curve generator and the
+// launchers of its kernels (one translation unit per stage).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/agnlc.h"
+#include "lc_common.cuh"
+
+namespace lc {
+
+// Curves of one length N = 2^log2n; every launch of the multi-kernel path
+// covers one class.
+struct ClassInfo {
+    uint32_t log2n = 0;
+    int ncurves = 0;
+    int* d_curves = nullptr;           // curve indices (device)
+    std::vector<int> h_curves;
+    void* d_tw = nullptr;              // e^{-2 pi i k/N}, k < N/2, element type cplx<T>
+    std::vector<int> radices;          // complex FFT passes (product N/2)
+    int tiles_per_curve = 0;           // sort tiles
+    int tile_len = 0;
+    int nchunks = 0;                   // scan chunks of tiles
+    size_t hist_off = 0;               // into d_hist (u32)
+    size_t cbase_off = 0;              // into d_cbase (u32)
+    size_t partial_off = 0;            // into d_partial (double)
+    bool resident = false;             // iterated by the fused on-chip kernel
+};
+
+struct Plan {
+    int device = 0;
+    lc_precision prec = LC_FP32;
+    size_t ncurves = 0;
+    size_t total = 0;        // sum N
+    size_t total_h = 0;      // sum (N/2 + 1)
+    uint32_t max_iters = 0;
+    std::vector<lc_job> jobs;
+    std::vector<CurveDev> h_curves;
+    std::vector<ClassInfo> classes;
+
+    // device memory (one arena)
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    CurveDev* d_curves = nullptr;
+    ErdfConst* d_erdf = nullptr;
+    double* d_sigma = nullptr;
+    double* d_partial = nullptr;
+    uint32_t* d_eff_iters = nullptr;
+    int* d_iter = nullptr;
+    void* d_x = nullptr;       // state, sum N (T)
+    void* d_f = nullptr;       // FFT ping-pong, sum N (T)
+    void* d_A = nullptr;       // amplitudes, sum (N/2+1) (T)
+    void* d_s = nullptr;       // sorted draws, sum N (T)
+    void* d_keysA = nullptr;   // sort keys (K), sum N
+    void* d_keysB = nullptr;
+    uint32_t* d_valsA = nullptr;
+    uint32_t* d_valsB = nullptr;
+    double2* d_spec = nullptr; // FP64 TK spectrum (setup only; aliases the sort buffers)
+    uint32_t* d_hist = nullptr;
+    uint32_t* d_cbase = nullptr;
+    size_t tw_bytes = 0;
+    void* d_tk_stage = nullptr;  // lazily allocated for lc_generate_host
+
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t t_setup0 = nullptr, t_setup1 = nullptr, t_it0 = nullptr, t_it1 = nullptr;
+    bool timed_setup = false, timed_iter = false;
+    cudaGraphExec_t iter_graph = nullptr;
+    uint64_t launches_per_iter = 0;
+    uint64_t last_launches = 0;
+    bool setup_done = false;
+    bool use_resident = true;
+};
+
+// setup stage (lc_setup.cu)
+int spec_blocks_per_curve(uint32_t log2n);
+void launch_tk_spectrum(const Plan& p, const ClassInfo& k, cudaStream_t st);
+template <typename T> void launch_amplitudes(const Plan& p, const ClassInfo& k, cudaStream_t st);
+void launch_erdf_constants(const Plan& p, cudaStream_t st);
+template <typename T> void launch_erdf_draws(const Plan& p, const ClassInfo& k, cudaStream_t st);
+
+// FFT stage (lc_fft.cu)
+std::vector<int> fft_radices(uint32_t log2m);
+template <typename T> void launch_twiddles(const ClassInfo& k, cudaStream_t st);
+// Complex FFT of every curve of the class (forward: e^{-}, inverse: e^{+}),
+// ping-ponging between `in` and `other`; the last pass writes `final_out`
+// when it is non-null.  Returns the buffer that holds the result.  When
+// `gated` the kernels skip curves whose iteration budget is spent.
+template <typename T> void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in,
+                                       void* other, void* final_out, bool gated, cudaStream_t st,
+                                       uint64_t* launches);
+template <typename T> void launch_spectral_iter(const Plan& p, const ClassInfo& k, const void* Z,
+                                                void* Zp, cudaStream_t st);
+template <typename T> void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_t st);
+
+// sort stage (lc_sort.cu)
+constexpr int kSortTile = 2048;
+constexpr int kScanChunk = 32;
+enum SortMode { kSortArgsortScatter = 1, kSortKeysToValues = 2 };
+// Stable LSD radix sort of each curve's values `src` (order keys of T):
+// kSortArgsortScatter writes x[perm[r]] = s[r]; kSortKeysToValues writes the
+// sorted values to s.
+template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode,
+                                       bool gated, cudaStream_t st, uint64_t* launches);
+
+// fused on-chip iteration (lc_resident.cu)
+bool resident_supported(const Plan& p, uint32_t log2n);
+// Runs n_it iterations (from the plan's current iteration index) of every
+// curve of a resident class in one launch.
+void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStream_t st, uint64_t* launches);
+
+void launch_iter_increment(const Plan& p, cudaStream_t st);
+void launch_iter_add(const Plan& p, uint32_t n, cudaStream_t st);
+void launch_eff_iters(const Plan& p, uint32_t override_iters, cudaStream_t st);
+
+void set_error(const std::string& msg);
+const char* last_error_text();
+lc_status validate_job(const lc_job& j);
+
+// plan life cycle shared by the batch ABI and the server
+lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device, Plan** out);
+lc_status plan_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* launches);
+// n_it more iterations from the current iteration index (each curve stops at
+// its own job count)
+lc_status plan_continue(Plan& p, uint32_t n_it, cudaStream_t st, uint64_t* launches);
+void plan_free(Plan* p);
+
+}  // namespace lc

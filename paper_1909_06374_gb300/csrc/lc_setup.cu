@@ -1,0 +1,176 @@
+// lc_setup.cu -- setup stage of the generator (Sec. 2.1, first two steps):
+// TK95 spectrum of the Eq. 3 PSD, its FP64 variance, the target amplitudes,
+// and the ERDF draws by inverse CDF.
+#include "lc_internal.h"
+
+namespace lc {
+
+constexpr int kSpecBlock = 256;
+constexpr int kSpecPerThread = 4;
+constexpr int kSpecTile = kSpecBlock * kSpecPerThread;  // bins per block
+
+// TK95 (Sec. 2.1; Sec. 3.2.5): f_j = j/(N dt) (App. A), P_j from Eq. 3 with
+// A = 1, X_0 = 0, X_j = sqrt(P_j/2)(g_re + i g_im) for 0 < j < N/2 and the
+// real Nyquist bin sqrt(P_{N/2}) g_re; g from Box-Muller on the two uniforms
+// of Philox block j (stream 0).  Also the block's share of
+// sigma^2 = X_{N/2}^2 + 2 sum_{0<j<N/2} |X_j|^2 (Parseval for the
+// unnormalised inverse transform), reduced in a fixed order.
+__global__ void __launch_bounds__(kSpecBlock)
+k_tk_spectrum(const CurveDev* __restrict__ curves, const int* __restrict__ cls_curves,
+              int blocks_per_curve, double2* __restrict__ spec, double* __restrict__ partial)
+{
+    const int ci = blockIdx.x / blocks_per_curve;
+    const int jb = blockIdx.x % blocks_per_curve;
+    const CurveDev cv = curves[cls_curves[ci]];
+    const uint64_t nh = 1ull << (cv.log2n - 1);
+    const double nd = (double)(1ull << cv.log2n);
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < kSpecPerThread; ++q) {
+        const uint64_t j = (uint64_t)jb * kSpecTile + (uint64_t)q * kSpecBlock + threadIdx.x;
+        if (j > nh) continue;
+        double2 X = make_double2(0.0, 0.0);
+        if (j > 0) {
+            const uint4 w = philox(j, cv.curve_id, 0u, cv.seed);
+            const double U1 = unit_open(w.x, w.y), U2 = unit_open(w.z, w.w);
+            const double rad = sqrt(-2.0 * log(U1));
+            double sn, cs;
+            sincospi(2.0 * U2, &sn, &cs);
+            const double f = (double)j / (nd * cv.dt);
+            const double y = f / cv.f_br;
+            const double P = 1.0 / (pow(y, cv.a_lo) + pow(y, cv.a_hi));
+            if (j < nh) {
+                const double a = sqrt(P * 0.5);
+                X = make_double2(a * rad * cs, a * rad * sn);
+                acc += 2.0 * (X.x * X.x + X.y * X.y);
+            } else {
+                X = make_double2(sqrt(P) * rad * cs, 0.0);
+                acc += X.x * X.x;
+            }
+        }
+        spec[cv.offh + j] = X;
+    }
+    __shared__ double red[kSpecBlock];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kSpecBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// sigma of each curve of a class: its partial sums added in block order.
+__global__ void k_sigma(const int* __restrict__ cls_curves, int ncurves, int blocks_per_curve,
+                        const double* __restrict__ partial, double* __restrict__ sigma)
+{
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= ncurves) return;
+    double s = 0.0;
+    for (int b = 0; b < blocks_per_curve; ++b) s += partial[(size_t)ci * blocks_per_curve + b];
+    sigma[cls_curves[ci]] = sqrt(s);
+}
+
+// Target amplitudes of the normalised TK95 series: A_j = |X_j| / sigma, A_0 = 0.
+template <typename T>
+__global__ void k_amplitudes(const CurveDev* __restrict__ curves, const int* __restrict__ cls_curves,
+                             int ncurves, uint32_t log2n, const double2* __restrict__ spec,
+                             const double* __restrict__ sigma, T* __restrict__ A)
+{
+    const uint64_t nh1 = (1ull << (log2n - 1)) + 1;
+    const uint64_t total = (uint64_t)ncurves * nh1;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(t / nh1);
+        const uint64_t j = t - (uint64_t)ci * nh1;
+        const int c = cls_curves[ci];
+        const uint64_t offh = curves[c].offh;
+        const double2 X = spec[offh + j];
+        const double a = j == 0 ? 0.0 : hypot(X.x, X.y) / sigma[c];
+        A[offh + j] = (T)a;
+    }
+}
+
+__global__ void k_erdf_constants(const CurveDev* __restrict__ curves, int ncurves, ErdfConst* __restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncurves) out[c] = erdf_constants(curves[c]);
+}
+
+// ERDF draws (Sec. 2.1 second step; inverse CDF instead of slice sampling):
+// draw k uses Philox block k/2 of stream 1, words (w0,w1) for even k and
+// (w2,w3) for odd k; lambda is computed in FP64 and rounded to T.
+template <typename T>
+__global__ void k_erdf_draws(const CurveDev* __restrict__ curves, const int* __restrict__ cls_curves,
+                             int ncurves, uint32_t log2n, const ErdfConst* __restrict__ ek,
+                             T* __restrict__ x)
+{
+    const uint64_t half = 1ull << (log2n - 1);
+    const uint64_t total = (uint64_t)ncurves * half;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(t >> (log2n - 1));
+        const uint64_t q = t & (half - 1);
+        const int c = cls_curves[ci];
+        const CurveDev& cv = curves[c];
+        const ErdfConst k = ek[c];
+        const uint4 w = philox(q, cv.curve_id, 1u, cv.seed);
+        const double l0 = erdf_draw(k, unit_open(w.x, w.y));
+        const double l1 = erdf_draw(k, unit_open(w.z, w.w));
+        x[cv.off + 2 * q] = (T)l0;
+        x[cv.off + 2 * q + 1] = (T)l1;
+    }
+}
+
+// ------------------------------------------------------------ launchers
+static int grid_for(uint64_t work, int block)
+{
+    uint64_t g = (work + block - 1) / block;
+    const uint64_t cap = 152ull * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+int spec_blocks_per_curve(uint32_t log2n)
+{
+    const uint64_t nh1 = (1ull << (log2n - 1)) + 1;
+    return (int)((nh1 + kSpecTile - 1) / kSpecTile);
+}
+
+void launch_tk_spectrum(const Plan& p, const ClassInfo& k, cudaStream_t st)
+{
+    const int bpc = spec_blocks_per_curve(k.log2n);
+    k_tk_spectrum<<<k.ncurves * bpc, kSpecBlock, 0, st>>>(p.d_curves, k.d_curves, bpc, p.d_spec,
+                                                         p.d_partial + k.partial_off);
+    k_sigma<<<(k.ncurves + 127) / 128, 128, 0, st>>>(k.d_curves, k.ncurves, bpc,
+                                                     p.d_partial + k.partial_off, p.d_sigma);
+}
+
+template <typename T>
+void launch_amplitudes(const Plan& p, const ClassInfo& k, cudaStream_t st)
+{
+    const uint64_t work = (uint64_t)k.ncurves * ((1ull << (k.log2n - 1)) + 1);
+    k_amplitudes<T><<<grid_for(work, 256), 256, 0, st>>>(p.d_curves, k.d_curves, k.ncurves, k.log2n,
+                                                         p.d_spec, p.d_sigma, (T*)p.d_A);
+}
+
+void launch_erdf_constants(const Plan& p, cudaStream_t st)
+{
+    k_erdf_constants<<<(int)((p.ncurves + 127) / 128), 128, 0, st>>>(p.d_curves, (int)p.ncurves, p.d_erdf);
+}
+
+template <typename T>
+void launch_erdf_draws(const Plan& p, const ClassInfo& k, cudaStream_t st)
+{
+    const uint64_t work = (uint64_t)k.ncurves << (k.log2n - 1);
+    k_erdf_draws<T><<<grid_for(work, 256), 256, 0, st>>>(p.d_curves, k.d_curves, k.ncurves, k.log2n,
+                                                         p.d_erdf, (T*)p.d_x);
+}
+
+template void launch_amplitudes<float>(const Plan&, const ClassInfo&, cudaStream_t);
+template void launch_amplitudes<double>(const Plan&, const ClassInfo&, cudaStream_t);
+template void launch_erdf_draws<float>(const Plan&, const ClassInfo&, cudaStream_t);
+template void launch_erdf_draws<double>(const Plan&, const ClassInfo&, cudaStream_t);
+
+}  // namespace lc

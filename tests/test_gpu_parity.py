@@ -1,0 +1,216 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+Bars (spec acceptance): ERDF draws and their multiset bit-exact; TK95
+stage within 2e-5 relative L2; one iteration from the same state equal per
+position except near ties (1e-5 rms of the oracle's pre-ranking series);
+FP64 runs equal end to end except near ties; runs deterministic."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_06374_gb300 import LC_FP32, LC_FP64, Plan, workloads
+from tests.parity import position_check, rank_stats, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TK_TOL = 2e-5
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def small_ragged(n=6, lo=4, hi=14, iters=4, seed=11):
+    rng = np.random.default_rng(seed)
+    jobs = workloads.ragged(ncurves=n, lo=lo, hi=hi, iters=iters, master_seed=seed)
+    # cover the smallest and a mid size explicitly
+    jobs[0]["log2n"] = lo
+    jobs[1]["log2n"] = hi
+    jobs[2]["log2n"] = 12
+    del rng
+    return jobs
+
+
+JOBSETS = {
+    "uniform_2^12": lambda: workloads.uniform(ncurves=8, log2n=12, iters=3),
+    "ragged_2^4..2^14": lambda: small_ragged(),
+    "long_2^20": lambda: workloads.long_curves(ncurves=2, log2n=20, iters=2),
+    "linear_space": lambda: [workloads.job(11, 2, seed=5, curve_id=9, linear_space=1)],
+}
+
+
+@pytest.mark.parametrize("name", list(JOBSETS))
+@pytest.mark.parametrize("prec", [LC_FP32, LC_FP64])
+def test_draws_bit_exact_and_sorted(name, prec):
+    jobs = JOBSETS[name]()
+    with Plan(jobs, prec) as p:
+        p.setup()
+        x0 = _np(p.buffer(0))
+        s = _np(p.buffer(2))
+    po = 0 if prec == LC_FP32 else 1
+    for c, j in enumerate(jobs):
+        n = 1 << j["log2n"]
+        erdf = oracle.job_params(j)[4:]
+        d = oracle.erdf_draws(erdf, n, j["seed"], j["curve_id"], prec=po, linear_space=j.get("linear_space", 0))
+        seg = slice(p.offsets[c], p.offsets[c + 1])
+        assert np.array_equal(x0[seg], d), (name, c)
+        assert np.array_equal(s[seg], np.sort(d)), (name, c)
+
+
+@pytest.mark.parametrize("name", list(JOBSETS))
+@pytest.mark.parametrize("prec", [LC_FP32, LC_FP64])
+def test_tk_stage_and_amplitudes(name, prec):
+    jobs = JOBSETS[name]()
+    with Plan(jobs, prec) as p:
+        tk = p.empty()
+        p.setup(out_tk=tk)
+        tk = _np(tk)
+        A = _np(p.buffer(1))
+    offh = 0
+    for c, j in enumerate(jobs):
+        n = 1 << j["log2n"]
+        par = oracle.job_params(j)
+        x_tk, A_or, _ = oracle.tk_series(j["log2n"], par[0], par[1:4], j["seed"], j["curve_id"])
+        err = rel_l2(tk[p.offsets[c]:p.offsets[c + 1]], x_tk)
+        assert err <= (TK_TOL if prec == LC_FP32 else 1e-12), (name, c, err)
+        a = A[offh:offh + n // 2 + 1]
+        offh += n // 2 + 1
+        assert a[0] == 0.0
+        assert rel_l2(a, A_or) <= (2e-7 if prec == LC_FP32 else 1e-13), (name, c)
+
+
+@pytest.mark.parametrize("name", list(JOBSETS))
+@pytest.mark.parametrize("prec", [LC_FP32, LC_FP64])
+@pytest.mark.parametrize("k", [0, 2])
+def test_one_iteration_from_the_same_state(name, prec, k):
+    """The oracle runs k iterations from its own setup; both sides then take one
+    iteration from that state (each with its own amplitudes and draws)."""
+    jobs = JOBSETS[name]()
+    po = 0 if prec == LC_FP32 else 1
+    states, expect = [], []
+    for j in jobs:
+        r = oracle.generate(dict(j, iters=0), prec=po, want=("x", "A", "s"))
+        xk, _, _ = oracle.iterate(r["A"], r["s"], r["x"], k)
+        x1, xa, _ = oracle.iterate(r["A"], r["s"], xk, 1, want_adj=True)
+        states.append(xk)
+        expect.append((x1, r["s"], xa))
+    with Plan(jobs, prec) as p:
+        p.setup()
+        st = torch.tensor(np.concatenate(states), dtype=p.dtype, device="cuda")
+        p.set_state(st)
+        p.iterate(1)
+        got = _np(p.get_state())
+    for c, (x1, s, xa) in enumerate(expect):
+        g = got[p.offsets[c]:p.offsets[c + 1]]
+        r = position_check(g, x1, s, xa)
+        assert r["not_in_draws"] == 0 and r["fail"] == 0, (name, c, r)
+
+
+def test_fp64_single_curve_end_to_end():
+    """The single-curve FP64 workload at full size (2^14 samples, 100 iterations)."""
+    jobs = workloads.single()
+    j = jobs[0]
+    with Plan(jobs, LC_FP64) as p:
+        g = _np(p.generate())
+    r = oracle.generate(dict(j, iters=0), prec=1, want=("x", "A", "s"))
+    x99, _, _ = oracle.iterate(r["A"], r["s"], r["x"], 99)
+    x100, xa, _ = oracle.iterate(r["A"], r["s"], x99, 1, want_adj=True)
+    assert np.array_equal(np.sort(g), r["s"])
+    res = position_check(g, x100, r["s"], xa)
+    stats = rank_stats(g, x100)
+    print("fp64 single curve:", res, stats)
+    assert res["fail"] == 0, (res, stats)
+
+
+@pytest.mark.parametrize("prec", [LC_FP32, LC_FP64])
+def test_end_to_end_multiset_and_rank_statistics(prec):
+    jobs = small_ragged(n=5, lo=10, hi=13, iters=20, seed=4)
+    po = 0 if prec == LC_FP32 else 1
+    with Plan(jobs, prec) as p:
+        g = _np(p.generate())
+    for c, j in enumerate(jobs):
+        r = oracle.generate(j, prec=po, want=("x", "s"))
+        seg = g[p.offsets[c]:p.offsets[c + 1]]
+        assert np.array_equal(np.sort(seg), r["s"])
+        st = rank_stats(seg, r["x"])
+        print(f"prec={prec} curve {c} N=2^{j['log2n']}: {st}")
+        assert st["spearman"] > 0.99
+
+
+def test_deterministic_and_independent_of_batch_mix():
+    jobs = small_ragged(n=6, lo=8, hi=14, iters=5, seed=21)
+    with Plan(jobs, LC_FP32) as p:
+        a = _np(p.generate())
+        b = _np(p.generate())
+    assert np.array_equal(a, b)
+    alone_job = jobs[3]
+    with Plan([alone_job], LC_FP32) as q:
+        alone = _np(q.generate())
+    assert np.array_equal(alone, a[p.offsets[3]:p.offsets[4]])
+
+
+def test_iterate_equals_generate():
+    jobs = workloads.uniform(ncurves=3, log2n=11, iters=6)
+    with Plan(jobs, LC_FP32) as p:
+        full = _np(p.generate())
+        p.setup()
+        p.iterate(2)
+        p.iterate(4)
+        split = _np(p.get_state())
+    assert np.array_equal(full, split)
+
+
+def test_zero_iterations_returns_draw_order():
+    jobs = [workloads.job(12, 0, seed=3, curve_id=1)]
+    with Plan(jobs, LC_FP32) as p:
+        g = _np(p.generate())
+    d = oracle.erdf_draws(oracle.job_params(jobs[0])[4:], 1 << 12, 3, 1, prec=0)
+    assert np.array_equal(g, d)
+
+
+def test_host_entry_point_matches_device():
+    from paper_1909_06374_gb300 import lc_generate_host
+    jobs = small_ragged(n=4, lo=9, hi=12, iters=3, seed=8)
+    with Plan(jobs, LC_FP32) as p:
+        dev = _np(p.generate())
+        tk_dev = p.empty()
+        p.setup(out_tk=tk_dev)
+        host = torch.empty(p.total, dtype=torch.float32).pin_memory()
+        host_tk = torch.empty(p.total, dtype=torch.float32).pin_memory()
+        lc_generate_host(p.handle, host, host_tk)
+        assert np.array_equal(host.numpy().astype(np.float64), dev)
+        assert np.array_equal(host_tk.numpy(), tk_dev.cpu().numpy())
+
+
+def test_uniform_full_size_sampled():
+    """4096 curves x 2^16, 200 iterations (the benchmark launch): the multiset of
+    64 sampled curves is the oracle's draw multiset, bit for bit, and one more
+    iteration from the oracle's state matches per position on 2 curves."""
+    jobs = workloads.uniform()
+    rng = np.random.default_rng(0)
+    sample = sorted(rng.choice(len(jobs), 64, replace=False).tolist())
+    step = sample[:2]
+    with Plan(jobs, LC_FP32) as p:
+        g = p.generate()
+        gn = g.cpu().numpy()
+        for c in sample:
+            j = jobs[c]
+            d = oracle.erdf_draws(oracle.job_params(j)[4:], 1 << 16, j["seed"], j["curve_id"], prec=0)
+            assert np.array_equal(np.sort(gn[p.offsets[c]:p.offsets[c + 1]].astype(np.float64)), np.sort(d))
+        # one-step check on sampled curves inside the full batch
+        st = g.clone()
+        expect = {}
+        for c in step:
+            j = jobs[c]
+            r = oracle.generate(dict(j, iters=0), prec=0, want=("x", "A", "s"))
+            xk, _, _ = oracle.iterate(r["A"], r["s"], r["x"], 1)
+            x1, xa, _ = oracle.iterate(r["A"], r["s"], xk, 1, want_adj=True)
+            st[p.offsets[c]:p.offsets[c + 1]] = torch.tensor(xk, dtype=torch.float32, device="cuda")
+            expect[c] = (x1, r["s"], xa)
+        p.set_state(st)
+        p.iterate(1)
+        got = p.get_state().cpu().numpy()
+    for c, (x1, s, xa) in expect.items():
+        r = position_check(got[p.offsets[c]:p.offsets[c + 1]], x1, s, xa)
+        assert r["fail"] == 0 and r["not_in_draws"] == 0, (c, r)
