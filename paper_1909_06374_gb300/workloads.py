@@ -102,3 +102,17 @@ def total_samples(jobs):
 
 def sample_iters(jobs):
     return sum((1 << j["log2n"]) * j["iters"] for j in jobs)
+
+
+def shard_jobs(jobs, world):
+    """Split a job list over `world` ranks, balancing the work sum N * iters
+    (longest-processing-time greedy).  Curves are independent, so ranks never
+    exchange data; every job lands on exactly one rank, in its original order."""
+    loads = [0] * world
+    owner = [0] * len(jobs)
+    order = sorted(range(len(jobs)), key=lambda i: -((1 << jobs[i]["log2n"]) * max(1, jobs[i]["iters"])))
+    for i in order:
+        r = min(range(world), key=lambda q: loads[q])
+        owner[i] = r
+        loads[r] += (1 << jobs[i]["log2n"]) * max(1, jobs[i]["iters"])
+    return [[jobs[i] for i in range(len(jobs)) if owner[i] == r] for r in range(world)]
