@@ -171,6 +171,28 @@ LC_API lc_status lc_plan_timing(lc_plan plan, float* setup_ms, float* iterate_ms
 /* Release the plan and its device memory (synchronises its stream). */
 LC_API lc_status lc_plan_destroy(lc_plan plan);
 
+/* ------------------------------------------------------- no allocation */
+
+/* Whole generator for ONE FP32 curve without allocating any device memory.
+ * There is no counterpart in the paper: this entry point exists for callers
+ * that cannot call cudaMalloc -- code that records into a CUDA stream
+ * capture, hosts whose device memory belongs to another allocator, or loops
+ * that must not allocate after start-up.  It runs the same kernels as
+ * lc_generate on a one-curve plan whose buffers all live in a 4 MiB
+ * file-scope device array of the library (held by every device that loads
+ * the library until the process exits).
+ *   job:    host pointer, read during the call; log2n must be <= 16 (larger
+ *           curves do not fit the array: LC_ERR_INVALID with a message).
+ *   out_x:  device pointer, 2^log2n floats, the final series (caller-owned).
+ *   stream: cudaStream_t (NULL = legacy default stream) of the current device.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array and leaves its
+ * contents behind (each call writes every buffer before reading it, so
+ * nothing needs clearing); calls whose work overlaps on the GPU, e.g. on two
+ * streams, race on the array and must be serialised by the caller. */
+LC_API lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A continuous-batching server on `device`: jobs submitted at any time are

@@ -59,6 +59,7 @@ _SIGS = {
     "lc_plan_last_launches": (c_i32, [c_p, ctypes.POINTER(c_u64)]),
     "lc_plan_timing": (c_i32, [c_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "lc_plan_destroy": (c_i32, [c_p]),
+    "lc_generate_noalloc": (c_i32, [ctypes.POINTER(LcJob), c_p, c_p]),
     "lc_server_create": (c_i32, [c_i32, c_sz, c_i32, ctypes.POINTER(c_p)]),
     "lc_submit": (c_i32, [c_p, ctypes.POINTER(LcJob), ctypes.POINTER(c_u64)]),
     "lc_poll": (c_i32, [c_p, c_u64, c_p, ctypes.POINTER(c_u64)]),
@@ -210,6 +211,11 @@ def lc_plan_timing(plan):
 
 def lc_plan_destroy(plan):
     _check(load().lc_plan_destroy(plan), "lc_plan_destroy")
+
+
+def lc_generate_noalloc(job, out_x, stream=None):
+    j = job if isinstance(job, LcJob) else make_job(job)
+    _check(load().lc_generate_noalloc(ctypes.byref(j), ptr(out_x), stream_ptr(stream)), "lc_generate_noalloc")
 
 
 def lc_server_create(device=0, hbm_budget_bytes=0, prec=LC_FP32):

@@ -1,0 +1,156 @@
+// lc_noalloc.cu -- single-curve generator entry point that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code running inside a CUDA stream
+// capture that must not add allocation nodes, embedders whose device memory is
+// owned by another allocator, or real-time loops that forbid allocation after
+// start-up.  lc_generate_noalloc runs the whole generator for one FP32 curve of
+// up to 2^16 samples with every intermediate buffer carved from one
+// file-scope device array; the caller passes only the job and the output.
+#include <mutex>
+
+#include "lc_internal.h"
+
+namespace lc {
+
+// Scratch of the allocation-free entry point: 4 MiB, enough for one FP32 curve
+// of 2^16 samples (state, FFT ping-pong, amplitudes, sorted draws, sort keys
+// and positions, histograms, twiddles, descriptors).  Every device that loads
+// the library holds it until the process exits.
+constexpr size_t kNoallocBytes = (size_t)4 << 20;
+constexpr uint32_t kNoallocMaxLog2 = 16;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[128];
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the symbol name is only a host-side handle).
+static lc_status noalloc_scratch(int dev, void** out)
+{
+    if (dev < 0 || dev >= 128) { set_error("device ordinal out of range"); return LC_ERR_INVALID; }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+            return LC_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LC_OK;
+}
+
+static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace lc
+
+using namespace lc;
+
+extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* stream)
+{
+    if (!job || !out_x) { set_error("null job or out_x"); return LC_ERR_INVALID; }
+    lc_status st = validate_job(*job);
+    if (st != LC_OK) return st;
+    if (job->log2n > kNoallocMaxLog2) {
+        set_error("lc_generate_noalloc: log2n above 16 exceeds the 4 MiB static scratch");
+        return LC_ERR_INVALID;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); set_error("no current CUDA device"); return LC_ERR_CUDA; }
+    void* base = nullptr;
+    st = noalloc_scratch(dev, &base);
+    if (st != LC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // one-curve plan whose buffers live in the static scratch
+    Plan p;
+    p.device = dev;
+    p.prec = LC_FP32;
+    p.ncurves = 1;
+    p.use_resident = true;
+    const size_t n = (size_t)1 << job->log2n, nh = n / 2 + 1, ts = 4;
+    CurveDev cv{};
+    cv.off = 0; cv.offh = 0; cv.log2n = job->log2n; cv.iters = job->iters;
+    cv.dt = job->dt; cv.f_br = job->psd.f_br; cv.a_lo = job->psd.alpha_low; cv.a_hi = job->psd.alpha_high;
+    cv.umin = job->erdf.log_lmin; cv.umax = job->erdf.log_lmax; cv.ub = job->erdf.log_lbreak;
+    cv.sl_lo = job->erdf.slope_low; cv.sl_hi = job->erdf.slope_high; cv.lin = job->erdf.linear_space ? 1 : 0;
+    cv.cls = 0; cv.seed = job->seed; cv.curve_id = job->curve_id;
+    p.h_curves.assign(1, cv);
+    p.total = n; p.total_h = nh; p.max_iters = job->iters;
+    p.classes.emplace_back();
+    ClassInfo& k = p.classes.back();
+    k.log2n = job->log2n;
+    k.ncurves = 1;
+    k.h_curves.assign(1, 0);
+    k.radices = fft_radices(k.log2n - 1);
+    k.tile_len = (int)(n < (size_t)kSortTile ? n : (size_t)kSortTile);
+    k.tiles_per_curve = (int)(n / k.tile_len);
+    k.nchunks = (k.tiles_per_curve + kScanChunk - 1) / kScanChunk;
+    k.resident = resident_supported(p, k.log2n);
+
+    char* b = (char*)base;
+    size_t at = 0;
+    auto take = [&](size_t bytes) { char* q = b + at; at = up256(at + bytes); return (void*)q; };
+    p.d_curves = (CurveDev*)take(sizeof(CurveDev));
+    p.d_erdf = (ErdfConst*)take(sizeof(ErdfConst));
+    p.d_sigma = (double*)take(sizeof(double));
+    p.d_eff_iters = (uint32_t*)take(sizeof(uint32_t));
+    p.d_iter = (int*)take(4 * sizeof(int));
+    p.d_partial = (double*)take(sizeof(double) * (size_t)spec_blocks_per_curve(k.log2n));
+    p.d_x = take(n * ts);
+    p.d_f = take(n * ts);
+    p.d_A = take(nh * ts);
+    p.d_s = take(n * ts);
+    const size_t sortbytes = std::max(2 * n * ts + 2 * n * 4, 16 * nh);
+    char* sortb = (char*)take(sortbytes);
+    p.d_keysA = sortb;
+    p.d_keysB = sortb + n * ts;
+    p.d_valsA = (uint32_t*)(sortb + 2 * n * ts);
+    p.d_valsB = (uint32_t*)(sortb + 2 * n * ts + n * 4);
+    p.d_spec = (double2*)sortb;
+    p.d_hist = (uint32_t*)take(sizeof(uint32_t) * (size_t)k.tiles_per_curve * 256);
+    p.d_cbase = (uint32_t*)take(sizeof(uint32_t) * (size_t)k.nchunks * 256);
+    k.d_tw = take((n / 2) * 2 * ts);
+    k.d_curves = (int*)take(sizeof(int));
+    if (at > kNoallocBytes) { set_error("lc_generate_noalloc: layout exceeds the static scratch"); return LC_ERR_INVALID; }
+
+    // descriptors (pageable host source: the copy is staged before the call returns)
+    const int zero = 0;
+    if (cudaMemcpyAsync(p.d_curves, &cv, sizeof(CurveDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(k.d_curves, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        set_error("descriptor upload failed");
+        return LC_ERR_CUDA;
+    }
+    launch_twiddles<float>(k, s);
+    // setup: TK95 spectrum and amplitudes, ERDF draws, sorted draws (Sec. 2.1)
+    launch_eff_iters(p, 0, s);
+    launch_tk_spectrum(p, k, s);
+    launch_amplitudes<float>(p, k, s);
+    launch_erdf_constants(p, s);
+    launch_erdf_draws<float>(p, k, s);
+    launch_sort<float>(p, k, p.d_x, kSortKeysToValues, false, s, nullptr);
+    // iterations (Sec. 3.2.2), launched directly (no graph)
+    if (job->iters > 0) {
+        if (k.resident) {
+            launch_resident(p, k, job->iters, s, nullptr);
+        } else {
+            for (uint32_t it = 0; it < job->iters; ++it) {
+                void* R1 = launch_fft<float>(p, k, false, p.d_x, p.d_f, nullptr, true, s, nullptr);
+                void* Zp = (R1 == p.d_x) ? p.d_f : p.d_x;
+                launch_spectral_iter<float>(p, k, R1, Zp, s);
+                void* R3 = launch_fft<float>(p, k, true, Zp, R1, nullptr, true, s, nullptr);
+                launch_sort<float>(p, k, R3, kSortArgsortScatter, true, s, nullptr);
+                launch_iter_increment(p, s);
+            }
+        }
+    }
+    if (cudaMemcpyAsync(out_x, p.d_x, n * ts, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        set_error("output copy failed");
+        return LC_ERR_CUDA;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error(std::string("lc_generate_noalloc: ") + cudaGetErrorString(e)); return LC_ERR_CUDA; }
+    return LC_OK;
+}
