@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--curves", type=int, default=NCURVES,
                     help="curves per GPU; anything but 4096 is a profiling case, not the bench workload")
+    ap.add_argument("--log2n", type=int, default=LOG2N,
+                    help="log2 of the curve length; anything but 16 is a profiling case")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "single", "long", "ragged", "serving"],
+                    help="uniform (default) is the benchmark line; the others are the remaining workloads")
+    ap.add_argument("--serving-seconds", type=float, default=60.0)
     return ap.parse_args()
 
 
@@ -59,8 +64,8 @@ def dist_info():
     return rank, world, local
 
 
-def jobs_for_rank(rank, ncurves=NCURVES):
-    jobs = workloads.uniform(ncurves=ncurves, log2n=LOG2N, iters=ITERS)
+def jobs_for_rank(rank, ncurves=NCURVES, log2n=LOG2N):
+    jobs = workloads.uniform(ncurves=ncurves, log2n=log2n, iters=ITERS)
     for j in jobs:
         j["seed"] += rank * ncurves
         j["curve_id"] += rank * ncurves
@@ -186,10 +191,28 @@ def run_gpu(args):
         lc_plan_last_launches, lc_plan_timing
     from paper_1909_06374_gb300 import _abi
 
-    jobs = jobs_for_rank(rank, args.curves)
-    samples = args.curves << LOG2N
-    sample_iters = samples * ITERS
-    plan = Plan(jobs, LC_FP32, device=local)
+    prec, dtype_name, desc = LC_FP32, "f32", None
+    if args.workload == "uniform":
+        jobs = jobs_for_rank(rank, args.curves, args.log2n)
+        if (args.curves, args.log2n) == (NCURVES, LOG2N):
+            desc = WORKLOAD
+        else:
+            desc = f"PROFILING CASE ({args.curves} curves x 2^{args.log2n}), not the bench workload"
+    elif args.workload == "single":
+        from paper_1909_06374_gb300 import LC_FP64
+        jobs, prec, dtype_name = workloads.single(), LC_FP64, "f64"
+        desc = "single curve: 1 x 2^14 samples, 100 E13 iterations, FP64 (latency)"
+    elif args.workload == "long":
+        jobs = workloads.shard_jobs(workloads.long_curves(), world)[rank]
+        desc = "long curves: 8 x 2^26 samples, dt = 7 d, per-curve f_br / high slope, 50 E13 iterations, FP32"
+    else:
+        jobs = workloads.shard_jobs(workloads.ragged(), world)[rank]
+        desc = ("ragged batch: 10000 curves, N log-uniform over 2^10..2^20, per-curve PSD and ERDF, "
+                "100 E13 iterations, FP32")
+    samples = workloads.total_samples(jobs)
+    sample_iters = workloads.sample_iters(jobs)
+    esize = 4 if prec == LC_FP32 else 8
+    plan = Plan(jobs, prec, device=local)
     out = plan.empty()
     stream = torch.cuda.current_stream()
 
@@ -228,14 +251,14 @@ def run_gpu(args):
     # end-to-end through the host entry point: job table in, series out
     e2e = None
     if not args.no_e2e:
-        host = torch.empty(samples, dtype=torch.float32).pin_memory()
+        host = torch.empty(samples, dtype=plan.dtype).pin_memory()
         jb = _abi.job_array(jobs)
         h2d = len(jobs) * _abi.ctypes.sizeof(_abi.LcJob)
         barrier()
         t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 2))
         for _ in range(e2e_steps):
-            h = lc_plan_create(jb, LC_FP32, local)
+            h = lc_plan_create(jb, prec, local)
             lc_generate_host(h, host, None, stream)
             lc_plan_destroy(h)
         barrier()
@@ -244,20 +267,21 @@ def run_gpu(args):
         if dist is not None:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": world * sample_iters * e2e_steps / float(te.item()), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": samples * 4,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": samples * esize,
                "what": "lc_plan_create (job table upload) + lc_generate_host (pinned output) + lc_plan_destroy"}
 
     peak, peak_kind = measured_peaks()
     it_ms = statistics.median(iter_ms)
-    alg_bytes = ALG_BYTES_PER_SAMPLE_ITER * sample_iters
+    alg_per = ALG_BYTES_PER_SAMPLE_ITER * (2 if prec != LC_FP32 else 1)
+    alg_bytes = alg_per * sample_iters
     achieved = alg_bytes / (it_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "kernel": "iteration stage (all E13 iterations of the batch)",
-            "peak_kind": peak_kind, "alg_bytes_per_sample_iter": ALG_BYTES_PER_SAMPLE_ITER,
+            "peak_kind": peak_kind, "alg_bytes_per_sample_iter": alg_per,
             "iterate_ms": it_ms}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload == "uniform":
         cores = os.cpu_count() or 1
         v, used, dt = cpu_baseline_run(cores, ITERS, cores)
         cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
@@ -267,10 +291,11 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.curves == NCURVES else
-                           f"PROFILING CASE ({args.curves} curves), not the bench workload", "curves_per_gpu": args.curves, "log2n": LOG2N, "iters": ITERS,
-                           "l2": "inputs larger than L2 (per-iteration working set > 2.5 GB)",
+                "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
+                "config": {"workload": desc, "curves_per_gpu": len(jobs), "samples_per_gpu": samples,
+                           "sample_iters_per_gpu": sample_iters,
+                           "l2": ("inputs larger than L2" if samples * esize * 3 > 129e6 else
+                                  "working set inside L2 (latency workload)"),
                            "parallelism": f"curves sharded over {world} GPU(s), no collective"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}
@@ -281,10 +306,97 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------ serving
+def run_serving(args):
+    """Poisson request stream (200 req/s) replayed in real time against (a) the
+    continuous-batching server and (b) the plain path that runs one job at a
+    time (plan, generate to host, destroy) in arrival order."""
+    import numpy as np
+    import torch
+    from paper_1909_06374_gb300 import (LC_FP32, lc_generate_host, lc_plan_create, lc_plan_destroy, lc_poll,
+                                        lc_server_create, lc_server_destroy, lc_submit)
+    from paper_1909_06374_gb300 import _abi
+    rank, world, local = dist_info()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    stream = workloads.serving_stream(duration=args.serving_seconds)
+    total_si = sum((1 << j["log2n"]) * j["iters"] for _, j in stream)
+    cap = 2.0 * args.serving_seconds + 60.0
+
+    def summarize(lat, done_si, makespan, unfinished):
+        lat = np.array(lat) if lat else np.array([np.nan])
+        return {"throughput": done_si / makespan, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "finished": int(len(lat) - np.isnan(lat).sum()),
+                "unfinished": unfinished, "makespan_s": makespan}
+
+    # (a) server
+    server = lc_server_create(local, 0, LC_FP32)
+    big = np.empty(1 << 24, dtype=np.float32)
+    lat, pending = [], {}
+    t0 = time.perf_counter()
+    i = 0
+    done_si = 0
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(stream) and stream[i][0] <= now:
+            t, j = stream[i]
+            tk = lc_submit(server, j)
+            pending[tk] = (j, t)
+            i += 1
+        for tk in list(pending):
+            j, t = pending[tk]
+            st, ns = lc_poll(server, tk, big)
+            if st == _abi.LC_OK:
+                lat.append(ns / 1e6)
+                done_si += (1 << j["log2n"]) * j["iters"]
+                del pending[tk]
+        if i >= len(stream) and not pending:
+            break
+        if now > cap:
+            break
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    lc_server_destroy(server)
+    srv = summarize(lat, done_si, makespan, len(pending) + len(stream) - i)
+
+    # (b) plain path, same stream, one job at a time
+    host = torch.empty(1 << 24, dtype=torch.float32).pin_memory()
+    lat2, done2 = [], 0
+    t0 = time.perf_counter()
+    k = 0
+    for t, j in stream:
+        now = time.perf_counter() - t0
+        if now > cap:
+            break
+        if now < t:
+            time.sleep(t - now)
+        h = lc_plan_create([j], LC_FP32, local)
+        lc_generate_host(h, host)
+        lc_plan_destroy(h)
+        lat2.append((time.perf_counter() - t0 - t) * 1e3)
+        done2 += (1 << j["log2n"]) * j["iters"]
+        k += 1
+    makespan2 = time.perf_counter() - t0
+    plain = summarize(lat2, done2, makespan2, len(stream) - k)
+    offered = total_si / args.serving_seconds
+    line = {"metric": "serving: light-curve samples x E13 iterations per second; p50/p99 latency",
+            "value": srv["throughput"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"Poisson 200 req/s for {args.serving_seconds:g} s, "
+                                                        "N log-uniform 2^12..2^24, iterations 20..200, per-job PSD/ERDF",
+                                            "jobs": len(stream), "offered_sample_iters_per_s": offered},
+            "server": srv, "plain_one_job_at_a_time": plain,
+            "server_saturated": srv["unfinished"] > 0 or srv["throughput"] < 0.95 * offered}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

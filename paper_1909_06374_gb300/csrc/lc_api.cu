@@ -8,6 +8,7 @@
 // CUDA graph per amplitude-adjustment iteration (Sec. 3.2.2).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -85,6 +86,12 @@ lc_status validate_job(const lc_job& j)
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+bool resident_allowed()
+{
+    const char* e = std::getenv("LC_PATH");
+    return !(e && std::strcmp(e, "multi") == 0);
+}
+
 template <typename T>
 static lc_status build_tables(Plan& p)
 {
@@ -112,6 +119,11 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->device = device;
     p->prec = prec;
     p->ncurves = njobs;
+    // Path selection (a tuning knob; results depend only on length and
+    // precision, never on the batch): LC_PATH=multi forces the multi-kernel
+    // iteration everywhere, LC_PATH=resident / auto (default) uses the fused
+    // on-chip kernels where they apply.
+    p->use_resident = resident_allowed();
     p->jobs.assign(jobs, jobs + njobs);
     const size_t ts = prec == LC_FP32 ? 4 : 8;
 
@@ -142,7 +154,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->total_h = offh;
 
     // arena layout
-    size_t hist = 0, cbase = 0, partial = 0, twb = 0;
+    size_t hist = 0, cbase = 0, partial = 0, twb = 0, rxb = 0;
     for (auto& k : p->classes) {
         k.ncurves = (int)k.h_curves.size();
         k.radices = fft_radices(k.log2n - 1);
@@ -154,6 +166,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         k.cbase_off = cbase; cbase += (size_t)k.ncurves * k.nchunks * 256;
         k.partial_off = partial; partial += (size_t)k.ncurves * spec_blocks_per_curve(k.log2n);
         twb += align_up((n / 2) * 2 * ts, 256);
+        rxb += align_up((size_t)k.ncurves * resident_exchange_floats(k.log2n) * 4, 256);
     }
     const size_t A256 = 256;
     size_t sz = 0;
@@ -174,6 +187,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     const size_t o_cbase = take(sizeof(uint32_t) * cbase);
     const size_t o_tw = take(twb);
     const size_t o_cls = take(sizeof(int) * njobs);
+    const size_t o_rx = prec == LC_FP32 ? take(rxb) : 0;
     p->arena_bytes = sz;
     if (cudaMalloc(&p->arena, sz) != cudaSuccess) {
         cudaGetLastError();
@@ -199,12 +213,17 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->d_spec = (double2*)(base + o_sort);
     p->d_hist = (uint32_t*)(base + o_hist);
     p->d_cbase = (uint32_t*)(base + o_cbase);
-    size_t tw_at = o_tw, cls_at = o_cls;
+    size_t tw_at = o_tw, cls_at = o_cls, rx_at = o_rx;
     for (auto& k : p->classes) {
         k.d_tw = base + tw_at;
         tw_at += align_up((((size_t)1 << k.log2n) / 2) * 2 * ts, 256);
         k.d_curves = (int*)(base + cls_at);
         cls_at += sizeof(int) * k.h_curves.size();
+        const size_t rx = prec == LC_FP32 ? (size_t)k.ncurves * resident_exchange_floats(k.log2n) * 4 : 0;
+        if (rx) {
+            k.d_rx = (float*)(base + rx_at);
+            rx_at += align_up(rx, 256);
+        }
     }
     p->tw_bytes = twb;
 

@@ -29,6 +29,7 @@ struct ClassInfo {
     size_t cbase_off = 0;              // into d_cbase (u32)
     size_t partial_off = 0;            // into d_partial (double)
     bool resident = false;             // iterated by the fused on-chip kernel
+    float* d_rx = nullptr;             // L2 exchange area of the cluster kernel (3 N floats per curve)
 };
 
 struct Plan {
@@ -109,6 +110,10 @@ template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const 
 
 // fused on-chip iteration (lc_resident.cu)
 bool resident_supported(const Plan& p, uint32_t log2n);
+// false when the environment forces the multi-kernel iteration (LC_PATH=multi)
+bool resident_allowed();
+// floats of cluster exchange area per curve of length 2^log2n (0: none needed)
+size_t resident_exchange_floats(uint32_t log2n);
 // Runs n_it iterations (from the plan's current iteration index) of every
 // curve of a resident class in one launch.
 void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStream_t st, uint64_t* launches);

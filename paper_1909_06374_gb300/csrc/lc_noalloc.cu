@@ -69,7 +69,7 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     p.device = dev;
     p.prec = LC_FP32;
     p.ncurves = 1;
-    p.use_resident = true;
+    p.use_resident = resident_allowed();
     const size_t n = (size_t)1 << job->log2n, nh = n / 2 + 1, ts = 4;
     CurveDev cv{};
     cv.off = 0; cv.offh = 0; cv.log2n = job->log2n; cv.iters = job->iters;
@@ -114,6 +114,7 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     p.d_cbase = (uint32_t*)take(sizeof(uint32_t) * (size_t)k.nchunks * 256);
     k.d_tw = take((n / 2) * 2 * ts);
     k.d_curves = (int*)take(sizeof(int));
+    if (resident_exchange_floats(k.log2n)) k.d_rx = (float*)take(resident_exchange_floats(k.log2n) * 4);
     if (at > kNoallocBytes) { set_error("lc_generate_noalloc: layout exceeds the static scratch"); return LC_ERR_INVALID; }
 
     // descriptors (pageable host source: the copy is staged before the call returns)

@@ -1,21 +1,24 @@
-// lc_resident.cu -- fused, on-chip amplitude-adjustment iterations (Sec. 3.2.2)
-// for curves whose working set fits in one CTA's shared memory.
+// lc_resident.cu -- fused, on-chip amplitude-adjustment iterations (Sec. 3.2.2).
 //
-// One CTA (N <= 2^14) or a cluster of C = N/2^14 CTAs (N = 2^15, 2^16) owns
-// one curve (FP32) for all the iterations of a launch: the state x stays in shared memory, the target
-// amplitudes A and the sorted draws s are read from L2 each iteration, and x
-// goes back to HBM once at the end.  Per iteration:
+// One CTA (N <= 2^14) or a cluster of C = N / 2^14 CTAs (N = 2^15, 2^16) owns
+// one FP32 curve for all the iterations of a launch.  Per iteration:
 //   1. complex Stockham FFT of z[m] = x[2m] + i x[2m+1] (M = N/2 points) in
-//      shared memory, radix-16 register butterflies, XOR-swizzled addresses;
-//   2. unpack to X_0..X_M, keep the phases, impose A, pack for the inverse
-//      (the pairs (k, M-k) are both local);
+//      shared memory: radix-16 register butterflies, XOR-swizzled addresses,
+//      twiddles from two small shared tables (W^t = W^{128 a} W^b);
+//   2. unpack to X_0..X_M, keep the phases, impose A, pack for the inverse;
 //   3. inverse complex FFT -> x_adj;
 //   4. stable LSD radix sort of the order keys of x_adj (4 passes of 8 bits;
-//      warp-level match + per-warp digit counts, block-wide scan), the last
-//      pass writing x[position] = s[rank] directly.
-// Shared memory: two complex buffers (2 x 2N bytes... 4N bytes each), two u16
-// index buffers (2N bytes each) and the per-warp digit counts (8 KB):
-// 12 N + 8 KB <= 204 KB at N = 2^14.
+//      ballot-based warp multisplit, per-warp digit counts, block-wide scan);
+//   5. x[position] = s[rank].
+// A and s stream from L2.  Single CTA: the state never leaves shared memory
+// until the end of the launch.  Cluster: the length-M transform is split
+// M = C x Mc (a cross-CTA radix-C step and local length-Mc transforms, CTA c
+// holding Z[C k + c]); the cross-CTA data goes through L2 -- on this GPU L2
+// moves ~10 TB/s between the SMs of a cluster against ~1-2.5 TB/s for
+// distributed shared memory -- in a per-curve exchange area, ordered by
+// cluster barriers (release/acquire).  Each CTA sorts its 2^14 keys locally
+// and merges ranks against the partners' published sorted keys; the rank
+// gather writes the next state straight into the curve's state array.
 #include <cooperative_groups.h>
 
 #include "lc_dft.cuh"
@@ -25,13 +28,23 @@ namespace lc {
 
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kResThreads = 512;
 constexpr int kResWarps = kResThreads / 32;
 constexpr uint32_t kResMinLog2 = 10;
-constexpr uint32_t kResMaxLog2 = 14;      // one CTA
-constexpr uint32_t kResClusterMaxLog2 = 16;  // clusters of 2 or 4 CTAs (16-bit positions)
+constexpr uint32_t kResMaxLog2 = 14;          // one CTA
+constexpr uint32_t kResClusterMaxLog2 = 16;   // clusters of 2 or 4 CTAs
+constexpr int kTwLo = 128;                    // low twiddle table (W^b, b < 128)
+constexpr int kTwHiMax = 64;                  // high table (W^{128 a}), Mc <= 8192
+constexpr size_t kWhBytes = (size_t)kResWarps * 256 * 4;
+constexpr size_t kTwBytes = (size_t)(kTwLo + kTwHiMax) * 8;
 
 __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 4) & 15); }
+// float index f of a swizzled complex buffer
+__device__ __forceinline__ int fsw(int f) { return (swz(f >> 1) << 1) | (f & 1); }
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
 // e^{-2 pi i k/N} for k in [0, N) from the class table rt (k < N/2).
 __device__ __forceinline__ float2 twN(const float2* __restrict__ rt, int k, int M)
@@ -41,11 +54,28 @@ __device__ __forceinline__ float2 twN(const float2* __restrict__ rt, int k, int 
     return make_float2(-w.x, -w.y);
 }
 
+// Shared twiddle tables of the local length-Mc transform: lo[b] = W_Mc^b,
+// hi[a] = W_Mc^{128 a}; W_Mc^t = e^{-2 pi i (t 2^log2ratio)/N}.
+__device__ __forceinline__ void build_tw(float2* lo, float2* hi, const float2* __restrict__ rt, int log2Mc,
+                                         int log2ratio, int M)
+{
+    const int Mc = 1 << log2Mc;
+    const int nhi = Mc > kTwLo ? Mc / kTwLo : 1;
+    for (int t = threadIdx.x; t < kTwLo + nhi; t += kResThreads) {
+        if (t < kTwLo) lo[t] = t < Mc ? twN(rt, t << log2ratio, M) : make_float2(1.f, 0.f);
+        else hi[t - kTwLo] = twN(rt, ((t - kTwLo) * kTwLo) << log2ratio, M);
+    }
+}
+
+__device__ __forceinline__ float2 tw_smem(const float2* lo, const float2* hi, int t)
+{
+    return cmulf(hi[t >> 7], lo[t & (kTwLo - 1)]);
+}
+
 // One radix-R Stockham pass of the length-Mc complex transform in shared memory.
-// W_Mc^t = e^{-2 pi i (N/Mc) t / N}.
 template <int R, bool INV>
 __device__ __forceinline__ void smem_pass(const float2* __restrict__ in, float2* __restrict__ out, int log2Mc,
-                                          int log2p, const float2* __restrict__ rt, int M, int log2ratio)
+                                          int log2p, const float2* lo, const float2* hi)
 {
     constexpr int LR = ilog2c(R);
     const int nb = 1 << (log2Mc - LR);
@@ -59,9 +89,9 @@ __device__ __forceinline__ void smem_pass(const float2* __restrict__ in, float2*
             const int step = k << (log2Mc - LR - log2p);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = twN(rt, (r * step) << log2ratio, M);
+                float2 w = tw_smem(lo, hi, r * step);
                 if (INV) w.y = -w.y;
-                u[r] = make_float2(u[r].x * w.x - u[r].y * w.y, u[r].x * w.y + u[r].y * w.x);
+                u[r] = cmulf(u[r], w);
             }
         }
         dft_regs<float, R, INV>(u);
@@ -71,25 +101,25 @@ __device__ __forceinline__ void smem_pass(const float2* __restrict__ in, float2*
     }
 }
 
-// Complex FFT of length Mc = 2^log2Mc held in shared memory (swizzled), ping-
+// Complex FFT of length 2^log2Mc held in shared memory (swizzled), ping-
 // ponging between a and b; returns the buffer holding the result.
 template <bool INV>
-__device__ float2* smem_fft(float2* a, float2* b, int log2Mc, const float2* __restrict__ rt, int M, int log2ratio)
+__device__ float2* smem_fft(float2* a, float2* b, int log2Mc, const float2* lo, const float2* hi)
 {
     int log2p = 0;
     float2* in = a;
     float2* out = b;
     const int rem = log2Mc & 3;
     if (rem) {
-        if (rem == 1) smem_pass<2, INV>(in, out, log2Mc, 0, rt, M, log2ratio);
-        else if (rem == 2) smem_pass<4, INV>(in, out, log2Mc, 0, rt, M, log2ratio);
-        else smem_pass<8, INV>(in, out, log2Mc, 0, rt, M, log2ratio);
+        if (rem == 1) smem_pass<2, INV>(in, out, log2Mc, 0, lo, hi);
+        else if (rem == 2) smem_pass<4, INV>(in, out, log2Mc, 0, lo, hi);
+        else smem_pass<8, INV>(in, out, log2Mc, 0, lo, hi);
         __syncthreads();
         log2p = rem;
         float2* t = in; in = out; out = t;
     }
     for (; log2p < log2Mc; log2p += 4) {
-        smem_pass<16, INV>(in, out, log2Mc, log2p, rt, M, log2ratio);
+        smem_pass<16, INV>(in, out, log2Mc, log2p, lo, hi);
         __syncthreads();
         float2* t = in; in = out; out = t;
     }
@@ -104,10 +134,26 @@ __device__ __forceinline__ float2 keep_phase_f(float2 X, float A)
     return make_float2(X.x * s, X.y * s);
 }
 
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// Z'_K from Z_K, Z_{M-K}: X_K = E + W O, X_{M-K} = conj(E - W O) with
+// E = (Z_K + conj Z_{M-K})/2, O = (Z_K - conj Z_{M-K})/(2i); Y = A X/|X|;
+// Z'_K = E' + i O', E' = Y_K + conj Y_{M-K}, O' = (Y_K - conj Y_{M-K}) conj W.
+// Called with the pair swapped and W -> -conj(W) it gives Z'_{M-K}.
+__device__ __forceinline__ float2 spectral_pair(float2 za, float2 zb, float2 W, float AK, float AMK)
+{
+    const float2 E = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+    const float2 O = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+    const float2 WO = cmulf(W, O);
+    const float2 XK = make_float2(E.x + WO.x, E.y + WO.y);
+    const float2 XMK = make_float2(E.x - WO.x, -(E.y - WO.y));
+    const float2 YK = keep_phase_f(XK, AK);
+    const float2 YMK = keep_phase_f(XMK, AMK);
+    const float2 Ep = make_float2(YK.x + YMK.x, YK.y - YMK.y);
+    const float2 Dd = make_float2(YK.x - YMK.x, YK.y + YMK.y);
+    const float2 Op = cmulf(Dd, make_float2(W.x, -W.y));
+    return make_float2(Ep.x - Op.y, Ep.y + Op.x);
+}
 
-// Spectral step on the local packed spectrum Z (length M): unpack, keep the
-// phases with amplitudes A, pack for the inverse transform into Zo.
+// Spectral step with every pair (k, M-k) local (single CTA).
 __device__ void spectral_local(const float2* __restrict__ Z, float2* __restrict__ Zo, const float* __restrict__ A,
                                const float2* __restrict__ rt, int M)
 {
@@ -125,24 +171,25 @@ __device__ void spectral_local(const float2* __restrict__ Z, float2* __restrict_
         } else {
             const float2 za = Z[swz(k)], zb = Z[swz(M - k)];
             const float2 W = __ldg(rt + k);
-            const float2 E = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-            const float2 O = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
-            const float2 WO = cmulf(W, O);
-            const float2 Xk = make_float2(E.x + WO.x, E.y + WO.y);
-            const float2 Xm = make_float2(E.x - WO.x, -(E.y - WO.y));
-            const float2 Yk = keep_phase_f(Xk, __ldg(A + k));
-            const float2 Ym = keep_phase_f(Xm, __ldg(A + M - k));
-            const float2 Ep = make_float2(Yk.x + Ym.x, Yk.y - Ym.y);
-            const float2 Dd = make_float2(Yk.x - Ym.x, Yk.y + Ym.y);
-            const float2 Op = cmulf(Dd, make_float2(W.x, -W.y));
-            Zo[swz(k)] = make_float2(Ep.x - Op.y, Ep.y + Op.x);
-            Zo[swz(M - k)] = make_float2(Ep.x + Op.y, -Ep.y + Op.x);
+            const float AK = __ldg(A + k), AMK = __ldg(A + M - k);
+            Zo[swz(k)] = spectral_pair(za, zb, W, AK, AMK);
+            Zo[swz(M - k)] = spectral_pair(zb, za, make_float2(-W.x, W.y), AMK, AK);
         }
     }
 }
 
-// float index f of a swizzled complex buffer
-__device__ __forceinline__ int fsw(int f) { return (swz(f >> 1) << 1) | (f & 1); }
+// Lanes of the warp holding the same 8-bit digit: eight ballots, one per bit
+// (the match instruction runs on a low-throughput pipe on this GPU).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d)
+{
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bal : ~bal;
+    }
+    return peers;
+}
 
 // Exclusive scan of v over threads 0..255 (called by all threads; others pass 0).
 __device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t* wsum)
@@ -170,41 +217,49 @@ struct ResArgs {
     const float* s;
     float* x;
     const float2* tw;
+    float* rx;           // cluster exchange area: 3 N floats per curve of the class
     uint32_t n_it;
     uint32_t log2n;
 };
 
-// One LSD radix pass over the L = N keys of the CTA.
-// FIRST: keys are the order keys of the x_adj floats in xa (swizzled view);
-// LAST: instead of the sorted pairs, writes xn[index] = s[rank].
-template <bool FIRST, bool LAST>
+// One stable LSD radix pass over the L = 2^LOG2L keys of the CTA (warp w
+// owns elements [w L/16, (w+1) L/16), lane-striped).  FIRST: keys are the
+// order keys of the x_adj floats in xa (swizzled); positions are implicit.
+// GATHER: instead of the sorted pairs, writes xn[position] = s[rank].
+// Ranking runs in two phases: the digits and ballot masks of all the warp's
+// slots (independent, so their ballot chains overlap), then the short chain
+// of per-warp digit counters in shared memory.
+template <int LOG2L, bool FIRST, bool GATHER>
 __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const uint32_t* __restrict__ kin,
                                            uint32_t* __restrict__ kout, const uint16_t* __restrict__ iin,
                                            uint16_t* __restrict__ iout, float* __restrict__ xn,
-                                           const float* __restrict__ s, int shift, int log2L, uint16_t* wh,
+                                           const float* __restrict__ s, int shift, uint32_t* wh,
                                            uint32_t* dbase, uint32_t* wsum)
 {
+    constexpr int EW = 1 << (LOG2L - 4);  // elements per warp
+    constexpr int SLOTS = EW >> 5;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int EW = 1 << (log2L - 4);  // elements per warp
-    const int slots = EW >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t rk[16];  // within-(warp, digit) ranks, two 16-bit values per register
+    uint32_t info[SLOTS];  // digit | below << 8 | count << 16
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        if (e < slots) {
-            const int el = w * EW + e * 32 + lane;
-            const uint32_t key = FIRST ? order_key(xa[fsw(el)]) : kin[el];
-            const uint32_t d = (key >> shift) & 255u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t below = __popc(peers & lt);
-            const uint32_t base = wh[w * 256 + d];
-            __syncwarp();
-            if (below == 0) wh[w * 256 + d] = (uint16_t)(base + __popc(peers));
-            __syncwarp();
-            const uint32_t r = base + below;
-            if (e & 1) rk[e >> 1] |= r << 16;
-            else rk[e >> 1] = r;
-        }
+    for (int e = 0; e < SLOTS; ++e) {
+        const int el = w * EW + e * 32 + lane;
+        const uint32_t key = FIRST ? order_key(xa[fsw(el)]) : kin[el];
+        const uint32_t d = (key >> shift) & 255u;
+        const uint32_t peers = digit_peers(d);
+        info[e] = d | ((uint32_t)__popc(peers & lt) << 8) | ((uint32_t)__popc(peers) << 16);
+    }
+    uint32_t rk[(SLOTS + 1) / 2];  // within-(warp, digit) ranks, two 16-bit values per register
+#pragma unroll
+    for (int e = 0; e < SLOTS; ++e) {
+        const uint32_t d = info[e] & 255u, below = (info[e] >> 8) & 255u;
+        const uint32_t base = wh[w * 256 + d];
+        __syncwarp();
+        if (below == 0) wh[w * 256 + d] = base + (info[e] >> 16);
+        __syncwarp();
+        const uint32_t r = base + below;
+        if (e & 1) rk[e >> 1] |= r << 16;
+        else rk[e >> 1] = r;
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -213,7 +268,7 @@ __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const u
 #pragma unroll
         for (int q = 0; q < kResWarps; ++q) {
             const uint32_t v = wh[q * 256 + d];
-            wh[q * 256 + d] = (uint16_t)tot;
+            wh[q * 256 + d] = tot;
             tot += v;
         }
     }
@@ -221,20 +276,17 @@ __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const u
     if (threadIdx.x < 256) dbase[threadIdx.x] = db;
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        if (e < slots) {
-            const int el = w * EW + e * 32 + lane;
-            const uint32_t key = FIRST ? order_key(xa[fsw(el)]) : kin[el];
-            const uint32_t d = (key >> shift) & 255u;
-            const uint32_t r = (e & 1) ? (rk[e >> 1] >> 16) : (rk[e >> 1] & 0xffffu);
-            const uint32_t dest = dbase[d] + wh[w * 256 + d] + r;
-            const uint32_t idx = FIRST ? (uint32_t)el : (uint32_t)iin[el];
-            if (LAST) {
-                xn[fsw((int)idx)] = __ldg(s + dest);
-            } else {
-                kout[dest] = key;
-                iout[dest] = (uint16_t)idx;
-            }
+    for (int e = 0; e < SLOTS; ++e) {
+        const int el = w * EW + e * 32 + lane;
+        const uint32_t d = info[e] & 255u;
+        const uint32_t r = (e & 1) ? (rk[e >> 1] >> 16) : (rk[e >> 1] & 0xffffu);
+        const uint32_t dest = dbase[d] + wh[w * 256 + d] + r;
+        const uint32_t idx = FIRST ? (uint32_t)el : (uint32_t)iin[el];
+        if (GATHER) {
+            xn[fsw((int)idx)] = __ldg(s + dest);
+        } else {
+            kout[dest] = FIRST ? order_key(xa[fsw(el)]) : kin[el];
+            iout[dest] = (uint16_t)idx;
         }
     }
     __syncthreads();
@@ -242,17 +294,21 @@ __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const u
     __syncthreads();
 }
 
+// ------------------------------------------------------------- one CTA
+template <int LOG2L>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident_cta(const ResArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int log2L = (int)a.log2n;
+    constexpr int log2L = LOG2L;
     const int L = 1 << log2L;
     const int M = L >> 1;
     float2* buf0 = (float2*)smem;
     float2* buf1 = (float2*)(smem + (size_t)4 * L);
     uint16_t* ia = (uint16_t*)(smem + (size_t)8 * L);
     uint16_t* ib = (uint16_t*)(smem + (size_t)10 * L);
-    uint16_t* wh = (uint16_t*)(smem + (size_t)12 * L);
+    uint32_t* wh = (uint32_t*)(smem + (size_t)12 * L);
+    float2* twlo = (float2*)(smem + (size_t)12 * L + kWhBytes);
+    float2* twhi = twlo + kTwLo;
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wsum[8];
 
@@ -267,7 +323,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_cta(const ResArgs a
     float* xg = a.x + cv.off;
 
     for (int q = threadIdx.x; q < kResWarps * 256; q += kResThreads) wh[q] = 0;
-    // state -> buf0 (complex view, swizzled)
+    build_tw(twlo, twhi, a.tw, log2L - 1, 1, M);
     const float2* xg2 = (const float2*)xg;
     for (int m = threadIdx.x; m < M; m += kResThreads) buf0[swz(m)] = xg2[m];
     __syncthreads();
@@ -275,19 +331,19 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_cta(const ResArgs a
     float2* z = buf0;
     float2* o = buf1;
     for (int it = 0; it < n_act; ++it) {
-        float2* Z = smem_fft<false>(z, o, log2L - 1, a.tw, M, 1);
+        float2* Z = smem_fft<false>(z, o, log2L - 1, twlo, twhi);
         float2* Zs = (Z == buf0) ? buf1 : buf0;
         spectral_local(Z, Zs, A, a.tw, M);
         __syncthreads();
-        float2* X = smem_fft<true>(Zs, Z, log2L - 1, a.tw, M, 1);
+        float2* X = smem_fft<true>(Zs, Z, log2L - 1, twlo, twhi);
         float2* other = (X == buf0) ? buf1 : buf0;
         uint32_t* kX = (uint32_t*)X;
         uint32_t* kO = (uint32_t*)other;
         // pass 0: x_adj (in X) -> keys in other; 1: other -> X; 2: X -> other; 3: other -> x in X
-        radix_pass<true, false>((const float*)X, nullptr, kO, nullptr, ia, nullptr, s, 0, log2L, wh, dbase, wsum);
-        radix_pass<false, false>(nullptr, kO, kX, ia, ib, nullptr, s, 8, log2L, wh, dbase, wsum);
-        radix_pass<false, false>(nullptr, kX, kO, ib, ia, nullptr, s, 16, log2L, wh, dbase, wsum);
-        radix_pass<false, true>(nullptr, kO, nullptr, ia, nullptr, (float*)X, s, 24, log2L, wh, dbase, wsum);
+        radix_pass<LOG2L, true, false>((const float*)X, nullptr, kO, nullptr, ia, nullptr, s, 0, wh, dbase, wsum);
+        radix_pass<LOG2L, false, false>(nullptr, kO, kX, ia, ib, nullptr, s, 8, wh, dbase, wsum);
+        radix_pass<LOG2L, false, false>(nullptr, kX, kO, ib, ia, nullptr, s, 16, wh, dbase, wsum);
+        radix_pass<LOG2L, false, true>(nullptr, kO, nullptr, ia, nullptr, (float*)X, s, 24, wh, dbase, wsum);
         z = X;
         o = other;
     }
@@ -295,25 +351,28 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_cta(const ResArgs a
     for (int m = threadIdx.x; m < M; m += kResThreads) xo2[m] = z[swz(m)];
 }
 
-
-// ---------------------------------------------------------------- clusters
-// A curve of N = C * L samples on a cluster of C CTAs; CTA c holds samples
-// [cL, (c+1)L).  The length-M (= N/2) complex transform is split as
-// M = C x Mc: a cross-CTA radix-C step (decimation in frequency forward,
-// in time inverse) reading the partners' blocks through distributed shared
-// memory, and local length-Mc transforms; CTA c then holds Z[C k + c].  The
-// spectral step reads Z[M - K] from the partner CTA (C - c) mod C.  The radix
-// sort is cluster-wide: per pass every CTA ranks its keys locally, the
-// per-CTA digit totals are exchanged, and each key is stored at its global
-// destination in the owning CTA's shared memory; the last pass stores
-// x[position] = s[rank] straight into the next state.
-namespace cg = cooperative_groups;
-
-template <int C>
-__device__ __forceinline__ float2 ld_cta(cg::cluster_group& cl, float2* local, int q, int me, int at)
+// ------------------------------------------------------------- clusters
+// First index i >= from with !(sorted[i] < key) (STRICT) or !(sorted[i] <= key),
+// i.e. the number of keys of sorted[0, n) below / not above `key`, given that
+// the first `from` keys already are: galloping probe, then binary search.
+template <bool STRICT>
+__device__ __forceinline__ int advance_count(const uint32_t* sorted, int n, int from, uint32_t key)
 {
-    if (q == me) return local[at];
-    return cl.map_shared_rank(local, q)[at];
+    int lo = from, step = 1;
+    while (lo + step <= n) {
+        const uint32_t v = sorted[lo + step - 1];
+        if (!(STRICT ? (v < key) : (v <= key))) break;
+        lo += step;
+        step <<= 1;
+    }
+    int hi = lo + step - 1 < n ? lo + step - 1 : n;  // answer in [lo, hi]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const uint32_t v = sorted[mid];
+        if (STRICT ? (v < key) : (v <= key)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 template <int C>
@@ -323,65 +382,62 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kResThreads, 1) k_re
     cg::cluster_group cl = cg::this_cluster();
     const int me = (int)cl.block_rank();
     constexpr int LOGC = ilog2c(C);
-    const int log2n = (int)a.log2n;
-    const int log2L = log2n - LOGC;
+    constexpr int log2L = (int)kResMaxLog2;  // every CTA holds 2^14 samples
     const int L = 1 << log2L;
     const int Mc = L >> 1;
     const int M = C * Mc;
+    const int N = 2 * M;
     float2* buf0 = (float2*)smem;
     float2* buf1 = (float2*)(smem + (size_t)4 * L);
     uint16_t* ia = (uint16_t*)(smem + (size_t)8 * L);
     uint16_t* ib = (uint16_t*)(smem + (size_t)10 * L);
-    uint16_t* wh = (uint16_t*)(smem + (size_t)12 * L);
+    uint32_t* wh = (uint32_t*)(smem + (size_t)12 * L);
+    float2* twlo = (float2*)(smem + (size_t)12 * L + kWhBytes);
+    float2* twhi = twlo + kTwLo;
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wsum[8];
-    __shared__ uint32_t ctot[256];
 
-    const int c = a.cls_curves[blockIdx.x / C];
+    const int ci = blockIdx.x / C;
+    const int c = a.cls_curves[ci];
     const CurveDev& cv = a.curves[c];
     const int it0 = *a.d_iter;
     int n_act = (int)a.eff_iters[c] - it0;
     if (n_act > (int)a.n_it) n_act = (int)a.n_it;
-    if (n_act <= 0) return;  // uniform over the cluster (same curve)
+    if (n_act <= 0) return;  // the same for every CTA of the cluster
     const float* A = a.A + cv.offh;
     const float* s = a.s + cv.off;
-    float* xg = a.x + cv.off + (size_t)me * L;
+    float* xs = a.x + cv.off;                             // state, all N samples
+    float2* gsp = (float2*)(a.rx + (size_t)ci * 3 * N);  // packed spectra (M complex)
+    float2* gu = gsp + M;                                 // inverse-step inputs (M complex)
+    uint32_t* gk = (uint32_t*)(gu + M);                  // sorted keys (N)
     const float2* rt = a.tw;
 
-    // W_C^{q me} for the cross-CTA steps
-    float2 wc[C];
+    float2 wc[C];  // W_C^{q me}
 #pragma unroll
-    for (int q = 0; q < C; ++q) wc[q] = twN(rt, ((q * me) % C) * (M * 2 / C), M);
-
+    for (int q = 0; q < C; ++q) wc[q] = twN(rt, ((q * me) % C) * (N / C), M);
     for (int q = threadIdx.x; q < kResWarps * 256; q += kResThreads) wh[q] = 0;
-    const float2* xg2 = (const float2*)xg;
-    for (int m = threadIdx.x; m < Mc; m += kResThreads) buf0[swz(m)] = xg2[m];
-    float2* z = buf0;
-    cl.sync();
+    build_tw(twlo, twhi, rt, log2L - 1, LOGC + 1, M);
+    __syncthreads();
 
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int EW = 1 << (log2L - 4);
-    const int slots = EW >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-
+    const float2* xs2 = (const float2*)xs;
+    const int pr = (C - me) % C;
     for (int it = 0; it < n_act; ++it) {
-        float2* y = (z == buf0) ? buf1 : buf0;
-        // forward cross-CTA radix-C step: y[m] = W_M^{m me} sum_q z_q[m] W_C^{q me}
+        // forward cross-CTA radix-C step from the state in L2:
+        // y[m] = W_M^{m me} sum_q z[q Mc + m] W_C^{q me}
         for (int m = threadIdx.x; m < Mc; m += kResThreads) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < C; ++q) {
-                const float2 v = ld_cta<C>(cl, z, q, me, swz(m));
-                const float2 t = cmulf(v, wc[q]);
+                const float2 t = cmulf(__ldcg(xs2 + q * Mc + m), wc[q]);
                 acc.x += t.x; acc.y += t.y;
             }
-            y[swz(m)] = cmulf(acc, twN(rt, 2 * m * me, M));
+            buf0[swz(m)] = cmulf(acc, twN(rt, 2 * m * me, M));
         }
-        cl.sync();  // partners done reading z before it is overwritten
-        float2* P = smem_fft<false>(y, z, log2L - 1, rt, M, LOGC + 1);
+        __syncthreads();
+        float2* P = smem_fft<false>(buf0, buf1, log2L - 1, twlo, twhi);  // Z[C k + me]
         float2* Q = (P == buf0) ? buf1 : buf0;
-        cl.sync();  // every Z block complete
-        const int pr = (C - me) % C;
+        for (int k = threadIdx.x; k < Mc; k += kResThreads) __stcg(gsp + me * Mc + k, P[swz(k)]);
+        cl.sync();  // every Z block published
         for (int k = threadIdx.x; k < Mc; k += kResThreads) {
             const int K = C * k + me;
             float2 out;
@@ -397,132 +453,79 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kResThreads, 1) k_re
                 out = make_float2(2.0f * Yh.x, -2.0f * Yh.y);
             } else {
                 const int kp = me == 0 ? Mc - k : Mc - 1 - k;
-                const float2 za = P[swz(k)];
-                const float2 zb = ld_cta<C>(cl, P, pr, me, swz(kp));
-                const float2 W = twN(rt, K, M);
-                const float2 E = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-                const float2 O = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
-                const float2 WO = cmulf(W, O);
-                const float2 XK = make_float2(E.x + WO.x, E.y + WO.y);
-                const float2 XMK = make_float2(E.x - WO.x, -(E.y - WO.y));
-                const float2 YK = keep_phase_f(XK, __ldg(A + K));
-                const float2 YMK = keep_phase_f(XMK, __ldg(A + M - K));
-                const float2 Ep = make_float2(YK.x + YMK.x, YK.y - YMK.y);
-                const float2 Dd = make_float2(YK.x - YMK.x, YK.y + YMK.y);
-                const float2 Op = cmulf(Dd, make_float2(W.x, -W.y));
-                out = make_float2(Ep.x - Op.y, Ep.y + Op.x);
+                const float2 zb = pr == me ? P[swz(kp)] : __ldcg(gsp + pr * Mc + kp);
+                out = spectral_pair(P[swz(k)], zb, twN(rt, K, M), __ldg(A + K), __ldg(A + M - K));
             }
             Q[swz(k)] = out;
         }
-        cl.sync();  // partners done reading P
-        float2* U = smem_fft<true>(Q, P, log2L - 1, rt, M, LOGC + 1);
+        __syncthreads();
+        float2* U = smem_fft<true>(Q, P, log2L - 1, twlo, twhi);
         float2* V = (U == buf0) ? buf1 : buf0;
-        cl.sync();  // every u block complete
+        for (int n = threadIdx.x; n < Mc; n += kResThreads) __stcg(gu + me * Mc + n, U[swz(n)]);
+        cl.sync();  // every u block published
         // inverse cross-CTA step: x_adj block me = sum_r e^{+2 pi i r me/C} e^{+2 pi i r n/M} u_r[n]
         for (int n = threadIdx.x; n < Mc; n += kResThreads) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int r = 0; r < C; ++r) {
-                const float2 v = ld_cta<C>(cl, U, r, me, swz(n));
+                const float2 v = r == me ? U[swz(n)] : __ldcg(gu + r * Mc + n);
                 const float2 tw = twN(rt, 2 * r * n, M);
                 const float2 t = cmulf(cmulf(v, make_float2(tw.x, -tw.y)), make_float2(wc[r].x, -wc[r].y));
                 acc.x += t.x; acc.y += t.y;
             }
             V[swz(n)] = acc;
         }
-        cl.sync();  // partners done reading U (it becomes a key buffer)
-
-        // cluster-wide stable LSD radix sort of the order keys of x_adj
+        __syncthreads();
+        // local stable sort of the block's keys (positions are local)
         uint32_t* kU = (uint32_t*)U;
         uint32_t* kV = (uint32_t*)V;
-#pragma unroll 1
-        for (int pass = 0; pass < 4; ++pass) {
-            const bool first = pass == 0, last = pass == 3;
-            const int shift = 8 * pass;
-            const uint32_t* kin = (pass == 1 || pass == 3) ? kU : kV;   // pass 0 reads floats from V
-            uint32_t* kout = (pass == 0 || pass == 2) ? kU : kV;
-            const uint16_t* iin = (pass == 2) ? ib : ia;
-            uint16_t* iout = (pass == 1) ? ib : ia;
-            const float* xa = (const float*)V;
-            uint32_t rk[16];
+        radix_pass<kResMaxLog2, true, false>((const float*)V, nullptr, kU, nullptr, ia, nullptr, s, 0, wh, dbase, wsum);
+        radix_pass<kResMaxLog2, false, false>(nullptr, kU, kV, ia, ib, nullptr, s, 8, wh, dbase, wsum);
+        radix_pass<kResMaxLog2, false, false>(nullptr, kV, kU, ib, ia, nullptr, s, 16, wh, dbase, wsum);
+        radix_pass<kResMaxLog2, false, false>(nullptr, kU, kV, ia, ib, nullptr, s, 24, wh, dbase, wsum);
+        // sorted keys in kV, positions in ib; publish the keys
+        for (int p = threadIdx.x; p < L; p += kResThreads) __stcg(gk + me * L + p, kV[p]);
+        cl.sync();  // every sorted block published
+        // global rank = local rank + keys of lower CTAs not above it + keys of
+        // higher CTAs below it (ties: lower position first, i.e. lower CTA first)
+        uint32_t gr[16];  // global ranks (< 2^16), two per register
+        const int per = L / kResThreads;  // consecutive sorted positions per thread
+#pragma unroll
+        for (int e = 0; e < 32; e += 2)
+            if (e < per) gr[e >> 1] = (uint32_t)(threadIdx.x * per + e) | ((uint32_t)(threadIdx.x * per + e + 1) << 16);
+        uint32_t* part = kU;  // free: holds a partner's sorted keys
+        for (int q = 0; q < C; ++q) {
+            if (q == me) continue;
+            for (int p = threadIdx.x; p < L; p += kResThreads) part[p] = __ldcg(gk + q * L + p);
+            __syncthreads();
+            int cnt = 0;
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
-                if (e < slots) {
-                    const int el = w * EW + e * 32 + lane;
-                    const uint32_t key = first ? order_key(xa[fsw(el)]) : kin[el];
-                    const uint32_t d = (key >> shift) & 255u;
-                    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-                    const uint32_t below = __popc(peers & lt);
-                    const uint32_t base = wh[w * 256 + d];
-                    __syncwarp();
-                    if (below == 0) wh[w * 256 + d] = (uint16_t)(base + __popc(peers));
-                    __syncwarp();
-                    const uint32_t r = base + below;
-                    if (e & 1) rk[e >> 1] |= r << 16;
-                    else rk[e >> 1] = r;
+                if (e < per) {
+                    const uint32_t key = kV[threadIdx.x * per + e];
+                    cnt = q < me ? advance_count<false>(part, L, cnt, key) : advance_count<true>(part, L, cnt, key);
+                    gr[e >> 1] += (uint32_t)cnt << ((e & 1) * 16);
                 }
             }
             __syncthreads();
-            if (threadIdx.x < 256) {
-                const int d = threadIdx.x;
-                uint32_t tot = 0;
-#pragma unroll
-                for (int q = 0; q < kResWarps; ++q) {
-                    const uint32_t v = wh[q * 256 + d];
-                    wh[q * 256 + d] = (uint16_t)tot;
-                    tot += v;
-                }
-                ctot[d] = tot;
-            }
-            cl.sync();  // every CTA's digit totals published
-            uint32_t all = 0, lower = 0;
-            if (threadIdx.x < 256) {
-#pragma unroll
-                for (int q = 0; q < C; ++q) {
-                    const uint32_t v = (q == me) ? ctot[threadIdx.x] : cl.map_shared_rank(ctot, q)[threadIdx.x];
-                    all += v;
-                    if (q < me) lower += v;
-                }
-            }
-            const uint32_t db = scan256(threadIdx.x < 256 ? all : 0u, wsum);
-            if (threadIdx.x < 256) dbase[threadIdx.x] = db + lower;
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                if (e < slots) {
-                    const int el = w * EW + e * 32 + lane;
-                    const uint32_t key = first ? order_key(xa[fsw(el)]) : kin[el];
-                    const uint32_t d = (key >> shift) & 255u;
-                    const uint32_t r = (e & 1) ? (rk[e >> 1] >> 16) : (rk[e >> 1] & 0xffffu);
-                    const uint32_t dest = dbase[d] + wh[w * 256 + d] + r;  // rank within the curve
-                    const uint32_t idx = first ? (uint32_t)(me * L + el) : (uint32_t)iin[el];
-                    if (last) {
-                        const float v = __ldg(s + dest);
-                        const int tq = (int)(idx >> log2L);
-                        const int pos = (int)(idx & (uint32_t)(L - 1));
-                        float* xs = (float*)V;  // next state
-                        if (tq == me) xs[fsw(pos)] = v;
-                        else cl.map_shared_rank(xs, tq)[fsw(pos)] = v;
-                    } else {
-                        const int tq = (int)(dest >> log2L);
-                        const int pos = (int)(dest & (uint32_t)(L - 1));
-                        if (tq == me) { kout[pos] = key; iout[pos] = (uint16_t)idx; }
-                        else {
-                            cl.map_shared_rank(kout, tq)[pos] = key;
-                            cl.map_shared_rank(iout, tq)[pos] = (uint16_t)idx;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            for (int q = threadIdx.x; q < kResWarps * 256; q += kResThreads) wh[q] = 0;
-            cl.sync();  // every remote store of this pass has landed
         }
-        z = V;
+        // rank-order replacement straight into the state in L2
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            if (e < per) {
+                const int p = threadIdx.x * per + e;
+                __stcg(xs + me * L + ib[p], __ldg(s + ((gr[e >> 1] >> ((e & 1) * 16)) & 0xffffu)));
+            }
+        }
+        cl.sync();  // the next state is complete
     }
-    float2* xo2 = (float2*)xg;
-    for (int m = threadIdx.x; m < Mc; m += kResThreads) xo2[m] = z[swz(m)];
-    cl.sync();
+}
+
+template <int LOG2L>
+void launch_cta(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
+{
+    cudaFuncSetAttribute(k_resident_cta<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    k_resident_cta<LOG2L><<<ncurves, kResThreads, smem, st>>>(a);
 }
 
 }  // namespace
@@ -530,6 +533,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kResThreads, 1) k_re
 bool resident_supported(const Plan& p, uint32_t log2n)
 {
     return p.use_resident && p.prec == LC_FP32 && log2n >= kResMinLog2 && log2n <= kResClusterMaxLog2;
+}
+
+size_t resident_exchange_floats(uint32_t log2n)
+{
+    return log2n > kResMaxLog2 && log2n <= kResClusterMaxLog2 ? (size_t)3 << log2n : 0;
 }
 
 void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStream_t st, uint64_t* launches)
@@ -543,15 +551,21 @@ void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStrea
     a.s = (const float*)p.d_s;
     a.x = (float*)p.d_x;
     a.tw = (const float2*)k.d_tw;
+    a.rx = k.d_rx;
     a.n_it = n_it;
     a.log2n = k.log2n;
     const int C = k.log2n <= kResMaxLog2 ? 1 : 1 << (k.log2n - kResMaxLog2);
     const size_t L = ((size_t)1 << k.log2n) / C;
-    const size_t smem = 12 * L + (size_t)kResWarps * 256 * 2;
-    const int smax = (int)(12 * ((size_t)1 << kResMaxLog2) + (size_t)kResWarps * 256 * 2);
+    const size_t smem = 12 * L + kWhBytes + kTwBytes;
+    const int smax = (int)(12 * ((size_t)1 << kResMaxLog2) + kWhBytes + kTwBytes);
     if (C == 1) {
-        cudaFuncSetAttribute(k_resident_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-        k_resident_cta<<<k.ncurves, kResThreads, smem, st>>>(a);
+        switch (k.log2n) {
+        case 10: launch_cta<10>(a, k.ncurves, smem, smax, st); break;
+        case 11: launch_cta<11>(a, k.ncurves, smem, smax, st); break;
+        case 12: launch_cta<12>(a, k.ncurves, smem, smax, st); break;
+        case 13: launch_cta<13>(a, k.ncurves, smem, smax, st); break;
+        default: launch_cta<14>(a, k.ncurves, smem, smax, st); break;
+        }
     } else if (C == 2) {
         cudaFuncSetAttribute(k_resident_cluster<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         k_resident_cluster<2><<<k.ncurves * 2, kResThreads, smem, st>>>(a);

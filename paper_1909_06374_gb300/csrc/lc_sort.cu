@@ -6,9 +6,10 @@
 // 4 passes for float, 8 for double); the payload is the position k in the
 // curve.  Each pass: per-tile digit histograms, a two-level scan (tiles in
 // chunks, then chunks) giving every (tile, digit) its output base, and a
-// stable scatter that ranks equal digits in element order (warp match +
-// per-warp counts).  The last pass of an argsort writes x[k] = s[rank]
-// directly instead of the sorted pairs.
+// stable scatter that ranks the tile in shared memory (ballot multisplit +
+// per-warp counts) and writes each digit's run with coalesced stores.  The
+// last pass of an argsort writes x[k] = s[rank] directly instead of the
+// sorted pairs.
 #include "lc_internal.h"
 
 namespace lc {
@@ -122,8 +123,27 @@ __global__ void __launch_bounds__(256) k_sort_scan_chunks(const SortArgs a)
     for (int ch = 0; ch < a.nchunks; ++ch) cb[(size_t)ch * 256] += digit_base;
 }
 
-// Stable scatter of one tile.  MODE 0: sorted (key, position) pairs;
-// kSortArgsortScatter: x[position] = s[rank]; kSortKeysToValues: s[rank] = value.
+// Lanes of the warp whose 8-bit digit equals this lane's: eight ballots.
+__device__ __forceinline__ uint32_t peers8(uint32_t d)
+{
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bal : ~bal;
+    }
+    return peers;
+}
+
+constexpr int kSlots = kSortTile / kSortThreads;  // elements per thread of a full tile
+
+// Stable scatter of one tile: the tile's elements are ranked in shared memory
+// (warp w owns elements [w T/8, (w+1) T/8), lane-striped; ballot multisplit
+// within the warp, per-warp digit counts, one block scan), placed in a
+// digit-sorted shared copy, and written out run by run, so that consecutive
+// threads write consecutive addresses of a digit's output range.
+// MODE 0: sorted (key, position) pairs; kSortArgsortScatter: x[position] =
+// s[rank]; kSortKeysToValues: s[rank] = value.
 template <typename T, bool FIRST, int MODE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
 {
@@ -132,53 +152,92 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
     const int t = blockIdx.x % a.tpc;
     const int c = a.cls_curves[ci];
     if (!curve_active(a, c)) return;
-    __shared__ uint32_t dbase[256];
-    __shared__ uint32_t running[256];
-    __shared__ uint32_t cnt[kSortWarps][256];
+    __shared__ K sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ uint32_t wcnt[kSortWarps][256];
+    __shared__ uint32_t ldstart[256];
+    __shared__ uint32_t gb[256];
+    __shared__ uint32_t wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    dbase[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
-                 a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
-    running[tid] = 0;
+    const int tl = a.tile_len;
+    const int EW = (tl + kSortWarps - 1) / kSortWarps;  // elements per warp
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) cnt[w][tid] = 0;
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][tid] = 0;
+    gb[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
+              a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
     __syncthreads();
     const uint64_t off = a.curves[c].off;
-    const uint32_t e0 = (uint32_t)t * (uint32_t)a.tile_len;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int j0 = 0; j0 < a.tile_len; j0 += kSortThreads) {
-        const bool valid = j0 + tid < a.tile_len;
-        const uint32_t e = e0 + j0 + tid;
-        K key = 0;
-        uint32_t val = 0, d = 0, peers = 0;
-        if (valid) {
-            key = load_key<T, FIRST>(a, off + e);
-            val = FIRST ? e : a.vals_in[off + e];
-            d = (uint32_t)(key >> a.shift) & 255u;
-        }
-        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        if (valid) peers = __match_any_sync(vmask, d);
-        const bool leader = valid && (lane == __ffs(peers) - 1);
-        if (leader) cnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pre = 0;
-            for (int w = 0; w < warp; ++w) pre += cnt[w][d];
-            const uint32_t dest = dbase[d] + running[d] + pre + __popc(peers & lt_mask);
-            if (MODE == 0) {
-                ((K*)a.keys_out)[off + dest] = key;
-                a.vals_out[off + dest] = val;
-            } else if (MODE == kSortArgsortScatter) {
-                ((T*)a.x_out)[off + val] = ((const T*)a.s_in)[off + dest];
-            } else {
-                ((T*)a.s_out)[off + dest] = key_value(key);
-            }
-        }
-        __syncthreads();
-        uint32_t tot = 0;
+    const uint32_t e0 = (uint32_t)t * (uint32_t)tl;
+    const uint32_t lt = (1u << lane) - 1u;
+    K key[kSlots];
+    uint32_t val[kSlots], rk[kSlots];
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) { tot += cnt[w][tid]; cnt[w][tid] = 0; }
-        running[tid] += tot;
-        __syncthreads();
+    for (int e = 0; e < kSlots; ++e) {
+        const int j = e * 32 + lane;              // index within the warp's elements
+        const int el = warp * EW + j;             // index within the tile
+        const bool valid = j < EW && el < tl;
+        K k = 0;
+        uint32_t v = 0, d = 0;
+        if (valid) {
+            k = load_key<T, FIRST>(a, off + e0 + el);
+            v = FIRST ? e0 + el : a.vals_in[off + e0 + el];
+            d = (uint32_t)(k >> a.shift) & 255u;
+        }
+        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+        const uint32_t peers = peers8(d) & vm;
+        const uint32_t below = __popc(peers & lt);
+        uint32_t base = 0;
+        if (valid) base = wcnt[warp][d];
+        __syncwarp();
+        if (valid && below == 0) wcnt[warp][d] = base + __popc(peers);
+        __syncwarp();
+        key[e] = k;
+        val[e] = v;
+        rk[e] = valid ? base + below : 0xffffffffu;
+    }
+    __syncthreads();
+    // per-digit prefix over warps (in place) and the tile's digit starts
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t v = wcnt[w][tid];
+        wcnt[w][tid] = tot;
+        tot += v;
+    }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int q = 0; q < warp; ++q) woff += wsum[q];
+    ldstart[tid] = woff + incl - tot;
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kSlots; ++e) {
+        if (rk[e] != 0xffffffffu) {
+            const uint32_t d = (uint32_t)(key[e] >> a.shift) & 255u;
+            const uint32_t lp = ldstart[d] + wcnt[warp][d] + rk[e];
+            sk[lp] = key[e];
+            sv[lp] = val[e];
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < tl; i += kSortThreads) {
+        const K k = sk[i];
+        const uint32_t d = (uint32_t)(k >> a.shift) & 255u;
+        const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
+        if (MODE == 0) {
+            ((K*)a.keys_out)[off + dest] = k;
+            a.vals_out[off + dest] = sv[i];
+        } else if (MODE == kSortArgsortScatter) {
+            ((T*)a.x_out)[off + sv[i]] = ((const T*)a.s_in)[off + dest];
+        } else {
+            ((T*)a.s_out)[off + dest] = key_value(k);
+        }
     }
 }
 

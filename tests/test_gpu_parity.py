@@ -214,3 +214,61 @@ def test_uniform_full_size_sampled():
     for c, (x1, s, xa) in expect.items():
         r = position_check(got[p.offsets[c]:p.offsets[c + 1]], x1, s, xa)
         assert r["fail"] == 0 and r["not_in_draws"] == 0, (c, r)
+
+
+def _one_step_in_batch(p, jobs, gpu_state, picks, prec=0):
+    """Replace the state of the picked curves by the oracle's state after one
+    oracle iteration, run one GPU iteration on the whole batch, and compare
+    the picked curves with the oracle's next iteration per position."""
+    st = gpu_state.clone()
+    expect = {}
+    for c in picks:
+        j = jobs[c]
+        r = oracle.generate(dict(j, iters=0), prec=prec, want=("x", "A", "s"))
+        xk, _, _ = oracle.iterate(r["A"], r["s"], r["x"], 1)
+        x1, xa, _ = oracle.iterate(r["A"], r["s"], xk, 1, want_adj=True)
+        st[p.offsets[c]:p.offsets[c + 1]] = torch.tensor(xk, dtype=p.dtype, device="cuda")
+        expect[c] = (x1, r["s"], xa)
+    p.set_state(st)
+    p.iterate(1)
+    got = p.get_state().cpu().numpy()
+    for c, (x1, s, xa) in expect.items():
+        r = position_check(got[p.offsets[c]:p.offsets[c + 1]], x1, s, xa)
+        assert r["fail"] == 0 and r["not_in_draws"] == 0, (c, jobs[c]["log2n"], r)
+
+
+def test_ragged_full_size_sampled():
+    """10000 curves, N log-uniform over 2^10..2^20, 100 iterations (the ragged
+    workload as benchmarked): draw multisets of 40 sampled curves bit-exact, and
+    one iteration from the oracle's state per position on curves of every path
+    (single-CTA, 2- and 4-CTA cluster, multi-kernel)."""
+    jobs = workloads.ragged()
+    rng = np.random.default_rng(1)
+    sample = sorted(rng.choice(len(jobs), 40, replace=False).tolist())
+    by_len = {}
+    for c, j in enumerate(jobs):
+        by_len.setdefault(j["log2n"], c)
+    picks = [by_len[l] for l in (10, 14, 15, 16, 17)]
+    with Plan(jobs, LC_FP32) as p:
+        g = p.generate()
+        gn = g.cpu().numpy()
+        for c in sample:
+            j = jobs[c]
+            d = oracle.erdf_draws(oracle.job_params(j)[4:], 1 << j["log2n"], j["seed"], j["curve_id"], prec=0)
+            seg = gn[p.offsets[c]:p.offsets[c + 1]].astype(np.float64)
+            assert np.array_equal(np.sort(seg), np.sort(d)), c
+        _one_step_in_batch(p, jobs, g, picks)
+
+
+def test_long_full_size_sampled():
+    """8 curves of 2^26 samples, 50 iterations: the draw multiset of two curves
+    is the oracle's, bit for bit (one iteration at 2^20 is checked per position
+    in test_one_iteration_from_the_same_state)."""
+    jobs = workloads.long_curves()
+    with Plan(jobs, LC_FP32) as p:
+        g = p.generate()
+        for c in (0, 5):
+            j = jobs[c]
+            d = oracle.erdf_draws(oracle.job_params(j)[4:], 1 << j["log2n"], j["seed"], j["curve_id"], prec=0)
+            seg = g[p.offsets[c]:p.offsets[c + 1]].cpu().numpy().astype(np.float64)
+            assert np.array_equal(np.sort(seg), np.sort(d)), c
