@@ -86,10 +86,13 @@ lc_status validate_job(const lc_job& j)
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-bool resident_allowed()
+int path_mode_from_env()
 {
     const char* e = std::getenv("LC_PATH");
-    return !(e && std::strcmp(e, "multi") == 0);
+    if (!e) return 0;
+    if (std::strcmp(e, "resident") == 0) return 1;
+    if (std::strcmp(e, "multi") == 0) return 2;
+    return 0;
 }
 
 template <typename T>
@@ -121,9 +124,9 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->ncurves = njobs;
     // Path selection (a tuning knob; results depend only on length and
     // precision, never on the batch): LC_PATH=multi forces the multi-kernel
-    // iteration everywhere, LC_PATH=resident / auto (default) uses the fused
-    // on-chip kernels where they apply.
-    p->use_resident = resident_allowed();
+    // iteration everywhere, LC_PATH=resident uses the fused kernels wherever
+    // they apply, the default follows the measured per-length table.
+    p->path_mode = path_mode_from_env();
     p->jobs.assign(jobs, jobs + njobs);
     const size_t ts = prec == LC_FP32 ? 4 : 8;
 

@@ -95,6 +95,120 @@ __global__ void __launch_bounds__(256) k_fft_pass(const PassArgs a)
     }
 }
 
+// One Stockham pass of radix R = 2^LR computed in shared memory over a tile
+// of kTileCols adjacent columns i0..i0+15 of one curve: the tile loads
+// u_r[i] = z[i + r M/R] (coalesced runs of 16 columns), applies W_{Rp}^{r k},
+// takes the R-point DFT of every column by radix-16 Stockham sub-passes in
+// shared memory (rows padded to 17 elements), and stores
+// y[(i-k)R + k + q p] (coalesced along i, or along q when p = 1).
+constexpr int kTileCols = 16;
+constexpr int kTileStride = kTileCols + 1;
+
+template <typename T, int Q, bool INV>
+__device__ __forceinline__ void tile_subpass(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int LR,
+                                             int log2p2, const cplx<T>* __restrict__ rt, uint64_t M, int log2M)
+{
+    using V = cplx<T>;
+    constexpr int LQ = ilog2c(Q);
+    const int R = 1 << LR;
+    const int nbq = R >> LQ;                 // butterflies per column
+    const int p2 = 1 << log2p2;
+    for (int b = threadIdx.x; b < nbq * kTileCols; b += 256) {
+        const int j = b & (kTileCols - 1);
+        const int i2 = b >> 4;
+        const int k2 = i2 & (p2 - 1);
+        V u[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) u[q] = in[(i2 + q * nbq) * kTileStride + j];
+        if (p2 > 1) {
+            // W_{Q p2}^{q k2} = W_M^{q k2 M/(Q p2)}
+            const uint64_t step = (uint64_t)k2 << (log2M - LQ - log2p2);
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                V w = twiddle_M<T>(rt, (uint64_t)q * step, M);
+                if (INV) w.y = -w.y;
+                u[q] = cmul(u[q], w);
+            }
+        }
+        dft_regs<T, Q, INV>(u);
+        const int jo = ((i2 - k2) << LQ) + k2;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) out[(jo + q * p2) * kTileStride + j] = u[q];
+    }
+}
+
+template <typename T, int LR, bool INV>
+__global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
+{
+    using V = cplx<T>;
+    constexpr int R = 1 << LR;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    V* b0 = (V*)tile_smem;
+    V* b1 = b0 + R * kTileStride;
+    const uint32_t log2nb = a.log2M - LR;
+    const int tpc = 1 << (log2nb - 4);       // tiles per curve (nb >= 16)
+    const int ci = blockIdx.x / tpc;
+    const int ti = blockIdx.x % tpc;
+    const int c = a.cls_curves[ci];
+    if (a.d_iter && (uint32_t)(*a.d_iter) >= a.eff_iters[c]) return;
+    const uint64_t base = a.curves[c].off >> 1;
+    const V* __restrict__ src = (const V*)a.in + base;
+    V* __restrict__ dst = (V*)a.out + base;
+    const V* __restrict__ rt = (const V*)a.tw;
+    const uint64_t nb = 1ull << log2nb;
+    const uint64_t p = 1ull << a.log2p;
+    const uint64_t M = 1ull << a.log2M;
+    const uint64_t i0 = (uint64_t)ti * kTileCols;
+    constexpr int PER = R * kTileCols / 256;  // elements per thread
+    V v[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {  // every load in flight before any use
+        const int idx = threadIdx.x + e * 256;
+        v[e] = src[i0 + (idx & (kTileCols - 1)) + (uint64_t)(idx >> 4) * nb];
+    }
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        const int idx = threadIdx.x + e * 256;
+        const int r = idx >> 4, j = idx & (kTileCols - 1);
+        V x = v[e];
+        if (p > 1) {
+            const uint64_t k = (i0 + j) & (p - 1);
+            V w = twiddle_M<T>(rt, ((uint64_t)r * k) << (a.log2M - LR - a.log2p), M);
+            if (INV) w.y = -w.y;
+            x = cmul(x, w);
+        }
+        b0[r * kTileStride + j] = x;
+    }
+    __syncthreads();
+    V* in = b0;
+    V* out = b1;
+    int log2p2 = 0;
+    constexpr int rem = LR & 3;
+    if (rem) {
+        tile_subpass<T, (1 << (rem ? rem : 1)), INV>(in, out, LR, 0, rt, M, a.log2M);
+        __syncthreads();
+        log2p2 = rem;
+        V* t = in; in = out; out = t;
+    }
+    for (; log2p2 < LR; log2p2 += 4) {
+        tile_subpass<T, 16, INV>(in, out, LR, log2p2, rt, M, a.log2M);
+        __syncthreads();
+        V* t = in; in = out; out = t;
+    }
+    if (p >= (uint64_t)kTileCols) {
+        for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
+            const int q = idx >> 4, j = idx & (kTileCols - 1);
+            const uint64_t i = i0 + j, k = i & (p - 1);
+            dst[((i - k) << LR) + k + (uint64_t)q * p] = in[q * kTileStride + j];
+        }
+    } else {  // p == 1: column i owns y[i R .. i R + R)
+        for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
+            const int j = idx >> LR, q = idx & (R - 1);
+            dst[((i0 + j) << LR) + q] = in[q * kTileStride + j];
+        }
+    }
+}
+
 // Phase kept, amplitude replaced: A X/|X|, and A (phase 0) when X = 0.
 __device__ __forceinline__ float2 keep_phase(float2 X, float A)
 {
@@ -266,10 +380,74 @@ static void launch_pass(int R, const PassArgs& a, uint64_t work, cudaStream_t st
     }
 }
 
+// Tile passes for a length-2^log2M transform (log2M >= 12): as few passes as
+// possible with at most 9 (float) or 8 (double) bits each -- the tile of
+// 2 x 2^bits x 17 elements must fit in shared memory -- bits spread evenly,
+// so every pass has between 5 and 9 bits.
+std::vector<int> tile_radices(uint32_t log2m, bool fp64)
+{
+    const int maxb = fp64 ? 8 : 9;
+    const int P = ((int)log2m + maxb - 1) / maxb;
+    std::vector<int> r;
+    for (int q = 0; q < P; ++q) r.push_back((int)log2m / P + (q < (int)log2m % P ? 1 : 0));
+    return r;
+}
+
+template <typename T, int LR, bool INV>
+static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
+{
+    const size_t smem = (size_t)2 * ((size_t)1 << LR) * kTileStride * sizeof(cplx<T>);
+    cudaFuncSetAttribute(k_fft_tile<T, LR, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fft_tile<T, LR, INV><<<blocks, 256, smem, st>>>(a);
+}
+
+template <typename T, bool INV>
+static void launch_tile(int LR, const PassArgs& a, int blocks, cudaStream_t st)
+{
+    switch (LR) {
+    case 5: launch_tile_lr<T, 5, INV>(a, blocks, st); break;
+    case 6: launch_tile_lr<T, 6, INV>(a, blocks, st); break;
+    case 7: launch_tile_lr<T, 7, INV>(a, blocks, st); break;
+    case 8: launch_tile_lr<T, 8, INV>(a, blocks, st); break;
+    default:
+        if (sizeof(T) == 4 && LR == 9) launch_tile_lr<float, 9, INV>(a, blocks, st);
+        else set_error("internal: unsupported tile radix");
+        break;
+    }
+}
+
 template <typename T>
 void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void* other, void* final_out,
                  bool gated, cudaStream_t st, uint64_t* launches)
 {
+    if (k.log2n - 1 >= 12) {
+        PassArgs a;
+        a.cls_curves = k.d_curves;
+        a.curves = p.d_curves;
+        a.eff_iters = p.d_eff_iters;
+        a.d_iter = gated ? p.d_iter : nullptr;
+        a.tw = k.d_tw;
+        a.ncurves = k.ncurves;
+        a.log2M = k.log2n - 1;
+        const std::vector<int> lr = tile_radices(a.log2M, sizeof(T) == 8);
+        uint32_t log2p = 0;
+        void* cur = in;
+        void* nxt = other;
+        for (size_t q = 0; q < lr.size(); ++q) {
+            a.in = cur;
+            a.out = (q + 1 == lr.size() && final_out) ? final_out : nxt;
+            a.log2p = log2p;
+            const int blocks = k.ncurves << (a.log2M - lr[q] - 4);
+            if (inverse) launch_tile<T, true>(lr[q], a, blocks, st);
+            else launch_tile<T, false>(lr[q], a, blocks, st);
+            if (launches) ++*launches;
+            log2p += (uint32_t)lr[q];
+            void* written = a.out;
+            nxt = cur;
+            cur = written;
+        }
+        return cur;
+    }
     PassArgs a;
     a.cls_curves = k.d_curves;
     a.curves = p.d_curves;

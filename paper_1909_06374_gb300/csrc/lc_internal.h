@@ -74,7 +74,7 @@ struct Plan {
     uint64_t launches_per_iter = 0;
     uint64_t last_launches = 0;
     bool setup_done = false;
-    bool use_resident = true;
+    int path_mode = 0;        // 0 auto (measured table), 1 resident where possible, 2 multi-kernel
 };
 
 // setup stage (lc_setup.cu)
@@ -110,8 +110,8 @@ template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const 
 
 // fused on-chip iteration (lc_resident.cu)
 bool resident_supported(const Plan& p, uint32_t log2n);
-// false when the environment forces the multi-kernel iteration (LC_PATH=multi)
-bool resident_allowed();
+// path mode from the environment: LC_PATH=resident -> 1, multi -> 2, else 0 (auto)
+int path_mode_from_env();
 // floats of cluster exchange area per curve of length 2^log2n (0: none needed)
 size_t resident_exchange_floats(uint32_t log2n);
 // Runs n_it iterations (from the plan's current iteration index) of every

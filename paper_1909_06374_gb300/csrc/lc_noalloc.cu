@@ -69,7 +69,7 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     p.device = dev;
     p.prec = LC_FP32;
     p.ncurves = 1;
-    p.use_resident = resident_allowed();
+    p.path_mode = path_mode_from_env();
     const size_t n = (size_t)1 << job->log2n, nh = n / 2 + 1, ts = 4;
     CurveDev cv{};
     cv.off = 0; cv.offh = 0; cv.log2n = job->log2n; cv.iters = job->iters;

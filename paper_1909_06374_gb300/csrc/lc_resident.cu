@@ -240,26 +240,31 @@ __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const u
     constexpr int SLOTS = EW >> 5;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t info[SLOTS];  // digit | below << 8 | count << 16
-#pragma unroll
-    for (int e = 0; e < SLOTS; ++e) {
-        const int el = w * EW + e * 32 + lane;
-        const uint32_t key = FIRST ? order_key(xa[fsw(el)]) : kin[el];
-        const uint32_t d = (key >> shift) & 255u;
-        const uint32_t peers = digit_peers(d);
-        info[e] = d | ((uint32_t)__popc(peers & lt) << 8) | ((uint32_t)__popc(peers) << 16);
-    }
+    constexpr int G = SLOTS < 8 ? SLOTS : 8;  // slots ranked per group (register budget)
     uint32_t rk[(SLOTS + 1) / 2];  // within-(warp, digit) ranks, two 16-bit values per register
 #pragma unroll
-    for (int e = 0; e < SLOTS; ++e) {
-        const uint32_t d = info[e] & 255u, below = (info[e] >> 8) & 255u;
-        const uint32_t base = wh[w * 256 + d];
-        __syncwarp();
-        if (below == 0) wh[w * 256 + d] = base + (info[e] >> 16);
-        __syncwarp();
-        const uint32_t r = base + below;
-        if (e & 1) rk[e >> 1] |= r << 16;
-        else rk[e >> 1] = r;
+    for (int g0 = 0; g0 < SLOTS; g0 += G) {
+        uint32_t info[G];  // digit | below << 8 | count << 16
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int el = w * EW + (g0 + q) * 32 + lane;
+            const uint32_t key = FIRST ? order_key(xa[fsw(el)]) : kin[el];
+            const uint32_t d = (key >> shift) & 255u;
+            const uint32_t peers = digit_peers(d);
+            info[q] = d | ((uint32_t)__popc(peers & lt) << 8) | ((uint32_t)__popc(peers) << 16);
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int e = g0 + q;
+            const uint32_t d = info[q] & 255u, below = (info[q] >> 8) & 255u;
+            const uint32_t base = wh[w * 256 + d];
+            __syncwarp();
+            if (below == 0) wh[w * 256 + d] = base + (info[q] >> 16);
+            __syncwarp();
+            const uint32_t r = base + below;
+            if (e & 1) rk[e >> 1] |= r << 16;
+            else rk[e >> 1] = r;
+        }
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -278,14 +283,15 @@ __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const u
 #pragma unroll
     for (int e = 0; e < SLOTS; ++e) {
         const int el = w * EW + e * 32 + lane;
-        const uint32_t d = info[e] & 255u;
+        const uint32_t key = FIRST ? order_key(xa[fsw(el)]) : kin[el];
+        const uint32_t d = (key >> shift) & 255u;
         const uint32_t r = (e & 1) ? (rk[e >> 1] >> 16) : (rk[e >> 1] & 0xffffu);
         const uint32_t dest = dbase[d] + wh[w * 256 + d] + r;
         const uint32_t idx = FIRST ? (uint32_t)el : (uint32_t)iin[el];
         if (GATHER) {
             xn[fsw((int)idx)] = __ldg(s + dest);
         } else {
-            kout[dest] = FIRST ? order_key(xa[fsw(el)]) : kin[el];
+            kout[dest] = key;
             iout[dest] = (uint16_t)idx;
         }
     }
@@ -530,9 +536,15 @@ void launch_cta(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream
 
 }  // namespace
 
+// Path table (measured on GB300, 2^28 samples x 200 iterations per length):
+// the fused kernels win from 2^10 to 2^15 (2.6x at 2^10, 1.8x at 2^14, 1.07x
+// at 2^15), the multi-kernel path at 2^16 (1.33x); LC_PATH=resident also
+// uses the 4-CTA cluster kernel at 2^16.
 bool resident_supported(const Plan& p, uint32_t log2n)
 {
-    return p.use_resident && p.prec == LC_FP32 && log2n >= kResMinLog2 && log2n <= kResClusterMaxLog2;
+    if (p.prec != LC_FP32 || log2n < kResMinLog2) return false;
+    if (p.path_mode == 2) return false;
+    return log2n <= (p.path_mode == 1 ? kResClusterMaxLog2 : kResClusterMaxLog2 - 1);
 }
 
 size_t resident_exchange_floats(uint32_t log2n)

@@ -81,13 +81,16 @@ __global__ void __launch_bounds__(256) k_sort_scan_tiles(const SortArgs a)
     if (!curve_active(a, c)) return;
     const int d = threadIdx.x;
     const int t0 = ch * kScanChunk;
-    const int t1 = min(a.tpc, t0 + kScanChunk);
+    const int nt = min(a.tpc, t0 + kScanChunk) - t0;
+    uint32_t* h = a.hist + ((size_t)ci * a.tpc + t0) * 256 + d;
+    uint32_t v[kScanChunk];  // all loads issued before the prefix (independent)
+#pragma unroll
+    for (int t = 0; t < kScanChunk; ++t) v[t] = t < nt ? h[(size_t)t * 256] : 0u;
     uint32_t run = 0;
-    uint32_t* h = a.hist + (size_t)ci * a.tpc * 256 + d;
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t v = h[(size_t)t * 256];
-        h[(size_t)t * 256] = run;
-        run += v;
+#pragma unroll
+    for (int t = 0; t < kScanChunk; ++t) {
+        if (t < nt) h[(size_t)t * 256] = run;
+        run += v[t];
     }
     a.cbase[((size_t)ci * a.nchunks + ch) * 256 + d] = run;
 }

@@ -272,3 +272,28 @@ def test_long_full_size_sampled():
             d = oracle.erdf_draws(oracle.job_params(j)[4:], 1 << j["log2n"], j["seed"], j["curve_id"], prec=0)
             seg = g[p.offsets[c]:p.offsets[c + 1]].cpu().numpy().astype(np.float64)
             assert np.array_equal(np.sort(seg), np.sort(d)), c
+
+
+@pytest.mark.parametrize("path", ["resident", "multi"])
+def test_forced_paths_one_step_at_2_16(path, monkeypatch):
+    """The per-length table picks one iteration path; both complete paths stay
+    correct: LC_PATH=resident runs 2^16 curves on the 4-CTA cluster kernel,
+    LC_PATH=multi runs 2^12 curves on the multi-kernel path."""
+    monkeypatch.setenv("LC_PATH", path)
+    log2n = 16 if path == "resident" else 12
+    jobs = workloads.uniform(ncurves=3, log2n=log2n, iters=2)
+    states, expect = [], []
+    for j in jobs:
+        r = oracle.generate(dict(j, iters=0), prec=0, want=("x", "A", "s"))
+        xk, _, _ = oracle.iterate(r["A"], r["s"], r["x"], 1)
+        x1, xa, _ = oracle.iterate(r["A"], r["s"], xk, 1, want_adj=True)
+        states.append(xk)
+        expect.append((x1, r["s"], xa))
+    with Plan(jobs, LC_FP32) as p:
+        p.setup()
+        p.set_state(torch.tensor(np.concatenate(states), dtype=torch.float32, device="cuda"))
+        p.iterate(1)
+        got = _np(p.get_state())
+    for c, (x1, s, xa) in enumerate(expect):
+        r = position_check(got[p.offsets[c]:p.offsets[c + 1]], x1, s, xa)
+        assert r["fail"] == 0 and r["not_in_draws"] == 0, (path, c, r)
