@@ -66,6 +66,8 @@ def lib():
                 "or_argsort": (None, [sz, P, P]),
                 "or_sort": (None, [sz, P]),
                 "or_iterate": (None, [u32, P, P, P, u32, P, P]),
+                "or_delta": (d, [sz, P, P]),
+                "or_iterate_conv": (u32, [u32, P, P, P, u32, d, P]),
                 "or_generate": (None, [u32, P, i32, u32, u64, u64, i32, P, P, P, P]),
                 "or_generate_batch": (i32, [sz, P, P, P, P, P, P, i32, i32, P]),
                 "or_spec_exp_v": (None, [sz, P, P]),
@@ -185,6 +187,23 @@ def iterate(A, s, x, iters, want_adj=False):
     lib().or_iterate(log2n, _p(A), _p(s), _p(x), iters,
                      _p(xa) if want_adj else None, _p(perm) if want_adj else None)
     return x, xa, perm
+
+
+def delta(x_old, x_new) -> float:
+    """Eq. 4: rms over the samples of log10(x_new / x_old)."""
+    a = _f64(x_old); b = _f64(x_new)
+    assert a.size == b.size
+    return float(lib().or_delta(a.size, _p(a), _p(b)))
+
+
+def iterate_conv(A, s, x, iters, thr=0.0):
+    """Iterations with the Sec. 3.2.2 stop: returns (x, deltas[:run], run)."""
+    x = _f64(x).copy(); A = _f64(A); s = _f64(s)
+    n = x.size; log2n = n.bit_length() - 1
+    assert 1 << log2n == n and A.size == n // 2 + 1 and s.size == n
+    d = np.full(max(int(iters), 1), np.nan)
+    run = int(lib().or_iterate_conv(log2n, _p(A), _p(s), _p(x), int(iters), float(thr), _p(d)))
+    return x, d[:run], run
 
 
 def job_params(job) -> np.ndarray:

@@ -444,6 +444,28 @@ OR_API void or_sort(size_t n, double* v) { qsort(v, n, sizeof(double), dbl_cmp);
 /* x is updated in place; x_adj (n doubles) receives the pre-ranking series   */
 /* and perm (n) the argsort of it when they are non-NULL.                   */
 /* ------------------------------------------------------------------------ */
+/* One iteration on n = 2^log2n samples; X (n/2+1 complex), xa (n) and perm
+ * (n) are work arrays that hold this iteration's spectrum, pre-ranking series
+ * and argsort afterwards. */
+static void iterate_once(size_t n, const double* A, const double* s, double* x,
+                         double* X, double* xa, int64_t* perm)
+{
+    size_t nh = n / 2;
+    or_r2c(n, x, X);
+    X[0] = A[0]; X[1] = 0.0;
+    for (size_t j = 1; j < nh; ++j) {
+        double re = X[2 * j], im = X[2 * j + 1];
+        double mag = hypot(re, im);
+        if (mag == 0.0) { X[2 * j] = A[j]; X[2 * j + 1] = 0.0; }
+        else { X[2 * j] = A[j] * (re / mag); X[2 * j + 1] = A[j] * (im / mag); }
+    }
+    X[2 * nh] = X[2 * nh] < 0.0 ? -A[nh] : A[nh];
+    X[2 * nh + 1] = 0.0;
+    or_c2r(n, X, xa);
+    or_argsort(n, xa, perm);
+    for (size_t r = 0; r < n; ++r) x[perm[r]] = s[r];
+}
+
 OR_API void or_iterate(uint32_t log2n, const double* A, const double* s, double* x,
                        uint32_t iters, double* x_adj_out, int64_t* perm_out)
 {
@@ -451,24 +473,52 @@ OR_API void or_iterate(uint32_t log2n, const double* A, const double* s, double*
     double* X = (double*)malloc(sizeof(double) * 2 * (nh + 1));
     double* xa = (double*)malloc(sizeof(double) * n);
     int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * n);
-    for (uint32_t it = 0; it < iters; ++it) {
-        or_r2c(n, x, X);
-        X[0] = A[0]; X[1] = 0.0;
-        for (size_t j = 1; j < nh; ++j) {
-            double re = X[2 * j], im = X[2 * j + 1];
-            double mag = hypot(re, im);
-            if (mag == 0.0) { X[2 * j] = A[j]; X[2 * j + 1] = 0.0; }
-            else { X[2 * j] = A[j] * (re / mag); X[2 * j + 1] = A[j] * (im / mag); }
-        }
-        X[2 * nh] = X[2 * nh] < 0.0 ? -A[nh] : A[nh];
-        X[2 * nh + 1] = 0.0;
-        or_c2r(n, X, xa);
-        or_argsort(n, xa, perm);
-        for (size_t r = 0; r < n; ++r) x[perm[r]] = s[r];
-    }
+    for (uint32_t it = 0; it < iters; ++it) iterate_once(n, A, s, x, X, xa, perm);
     if (x_adj_out && iters > 0) memcpy(x_adj_out, xa, sizeof(double) * n);
     if (perm_out && iters > 0) memcpy(perm_out, perm, sizeof(int64_t) * n);
     free(X); free(xa); free(perm);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Convergence distance of Sec. 3.2.2, Eq. 4, between consecutive iterates:  */
+/*   delta = rms_n [ log10( x_new(t_n) / x_old(t_n) ) ],  n = 1..N           */
+/* read as the root mean square about zero with the base-10 logarithm (the  */
+/* paper's "log" of Eddington ratios).  Both series must be positive.        */
+/* ------------------------------------------------------------------------ */
+OR_API double or_delta(size_t n, const double* x_old, const double* x_new)
+{
+    double acc = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        double t = log10(x_new[k] / x_old[k]);
+        acc += t * t;
+    }
+    return sqrt(acc / (double)n);
+}
+
+/* Iterations with the convergence test of Sec. 3.2.2: after iteration i     */
+/* (1-based) delta[i-1] = delta_i = Eq. 4 between x_{i-1} and x_i; the loop   */
+/* ends after the first i with delta_i < thr (strictly; thr <= 0 never ends  */
+/* it early) or after `iters`.  Returns the number of iterations run; x holds */
+/* the last iterate.                                                         */
+OR_API uint32_t or_iterate_conv(uint32_t log2n, const double* A, const double* s, double* x,
+                                uint32_t iters, double thr, double* delta)
+{
+    size_t n = (size_t)1 << log2n, nh = n / 2;
+    double* X = (double*)malloc(sizeof(double) * 2 * (nh + 1));
+    double* xa = (double*)malloc(sizeof(double) * n);
+    double* xp = (double*)malloc(sizeof(double) * n);
+    int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * n);
+    uint32_t it = 0;
+    while (it < iters) {
+        memcpy(xp, x, sizeof(double) * n);
+        iterate_once(n, A, s, x, X, xa, perm);
+        double d = or_delta(n, xp, x);
+        delta[it] = d;
+        ++it;
+        if (d < thr) break;
+    }
+    free(X); free(xa); free(xp); free(perm);
+    return it;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -250,7 +250,9 @@ __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const u
             const int el = w * EW + (g0 + q) * 32 + lane;
             const uint32_t key = FIRST ? order_key(xa[fsw(el)]) : kin[el];
             const uint32_t d = (key >> shift) & 255u;
-            const uint32_t peers = digit_peers(d);
+            // every third slot on the match pipe, the others on ballots: the two
+            // run on different pipes, which cut the pass time by ~10% here
+            const uint32_t peers = ((g0 + q) % 3 == 2) ? __match_any_sync(0xffffffffu, d) : digit_peers(d);
             info[q] = d | ((uint32_t)__popc(peers & lt) << 8) | ((uint32_t)__popc(peers) << 16);
         }
 #pragma unroll

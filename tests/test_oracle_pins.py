@@ -397,3 +397,99 @@ def test_batch_equals_single():
     assert used == 3
     single = np.concatenate([oracle.generate(j, prec=0)["x"] for j in jobs])
     assert np.array_equal(x, single)
+
+
+# --------------------------------------------------- convergence (Sec. 3.2.2)
+def test_delta_closed_forms():
+    """Eq. 4 on series with a known answer: identical series give 0; a
+    uniform factor c gives |log10 c| (base 10: c = 10 gives exactly 1, which a
+    natural log would miss); changing half the samples by 2 dex gives sqrt(2)
+    (mean over N, not N - 1); swapping two values a, b of N gives
+    sqrt(2/N)|log10(a/b)| (root of the mean of squares, not the mean of |.|)."""
+    x = 2.0 ** np.arange(-12, 4, dtype=np.float64)  # 16 exact powers of two
+    assert oracle.delta(x, x) == 0.0
+    assert oracle.delta(x, 10.0 * x) == 1.0
+    assert oracle.delta(x, 1000.0 * x) == pytest.approx(3.0, rel=1e-15)
+    assert oracle.delta(x, x / 100.0) == pytest.approx(2.0, rel=1e-15)
+    y = x.copy(); y[:8] *= 100.0
+    assert oracle.delta(x, y) == pytest.approx(math.sqrt(2.0), rel=1e-15)
+    z = x.copy(); z[[3, 11]] = z[[11, 3]]
+    want = math.sqrt(2.0 / 16.0) * abs(math.log10(x[3] / x[11]))
+    assert oracle.delta(x, z) == pytest.approx(want, rel=1e-14)
+
+
+def test_delta_symmetry_and_scale_invariance():
+    """The log ratio flips sign when the series are exchanged, and a common
+    factor cancels (Eq. 4 depends on ratios only)."""
+    rng = np.random.default_rng(11)
+    a = 10.0 ** rng.uniform(-4, 0, 1000)
+    b = rng.permutation(a)
+    d = oracle.delta(a, b)
+    assert d > 0
+    assert oracle.delta(b, a) == pytest.approx(d, rel=1e-14)
+    assert oracle.delta(7.5 * a, 7.5 * b) == pytest.approx(d, rel=1e-12)
+
+
+def _draw_state(log2n, seed=5):
+    j = workloads.job(log2n, 0, seed=seed, curve_id=1)
+    o = oracle.generate(j, prec=0, want=("x", "A", "s"))
+    return o["A"], o["s"], o["x"]
+
+
+def test_iterate_conv_records_consecutive_distances():
+    """delta_i compares iterate i with iterate i - 1 (x_0 = the draws in draw
+    order), checked against single iterations replayed one at a time; without
+    a threshold every iteration runs and the final state is the plain one."""
+    A, s, x0 = _draw_state(8)
+    xk, d, run = oracle.iterate_conv(A, s, x0, 6, 0.0)
+    assert run == 6 and d.shape == (6,)
+    prev = x0
+    for i in range(6):
+        cur, _, _ = oracle.iterate(A, s, prev, 1)
+        assert d[i] == oracle.delta(prev, cur)
+        prev = cur
+    assert np.array_equal(xk, prev)
+    plain, _, _ = oracle.iterate(A, s, x0, 6)
+    assert np.array_equal(xk, plain)
+
+
+def test_iterate_conv_threshold_stops_at_first_crossing():
+    """The run ends after the first i with delta_i < thr (strict), leaving x_i."""
+    A, s, x0 = _draw_state(8)
+    _, d, _ = oracle.iterate_conv(A, s, x0, 12, 0.0)
+    assert np.all(d >= 0)
+    # a threshold just above delta_k for the first k that is a new minimum
+    k = next(i for i in range(1, 12) if d[i] < d[:i].min())
+    thr = float(np.nextafter(d[k], np.inf))
+    xk, dk, run = oracle.iterate_conv(A, s, x0, 12, thr)
+    assert run == k + 1
+    assert np.array_equal(dk, d[:k + 1])
+    ref, _, _ = oracle.iterate(A, s, x0, k + 1)
+    assert np.array_equal(xk, ref)
+    # a threshold equal to delta_k does not stop there (strict comparison)
+    _, _, run2 = oracle.iterate_conv(A, s, x0, k + 1, float(d[k]))
+    assert run2 == k + 1
+    # an infinite threshold stops after the first iteration
+    _, d1, run1 = oracle.iterate_conv(A, s, x0, 12, math.inf)
+    assert run1 == 1 and d1[0] == d[0]
+
+
+def test_iterate_conv_fixed_point():
+    """Sec. 3.2.2 calls the iteration converged when the order of the values no
+    longer changes.  For N = 64 the E13 map reaches a fixed point: from there on
+    every delta is exactly 0, delta_i = 0 exactly when x_i = x_{i-1} (the draws
+    are distinct and positive), and a tiny positive threshold stops the run at
+    the first zero."""
+    A, s, x0 = _draw_state(6)
+    assert np.unique(s).size == s.size and s[0] > 0
+    xs = [x0]
+    for _ in range(60):
+        xs.append(oracle.iterate(A, s, xs[-1], 1)[0])
+    _, d, run = oracle.iterate_conv(A, s, x0, 60, 0.0)
+    assert run == 60
+    for i in range(60):
+        assert (d[i] == 0.0) == bool(np.array_equal(xs[i + 1], xs[i]))
+    zeros = np.nonzero(d == 0.0)[0]
+    assert zeros.size > 0 and np.all(d[zeros[0]:] == 0.0)
+    _, _, run_t = oracle.iterate_conv(A, s, x0, 60, 1e-300)
+    assert run_t == zeros[0] + 1
