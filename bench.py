@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "single", "long", "ragged", "serving"],
                     help="uniform (default) is the benchmark line; the others are the remaining workloads")
     ap.add_argument("--serving-seconds", type=float, default=60.0)
+    ap.add_argument("--convergence", type=float, default=None, metavar="THRESHOLD",
+                    help="run with the Eq. 4 convergence test on (every curve stops once delta < THRESHOLD; "
+                         "0 = measure delta without stopping); a variant line, not the bench workload")
     return ap.parse_args()
 
 
@@ -213,6 +216,9 @@ def run_gpu(args):
     sample_iters = workloads.sample_iters(jobs)
     esize = 4 if prec == LC_FP32 else 8
     plan = Plan(jobs, prec, device=local)
+    if args.convergence is not None:
+        plan.set_convergence([args.convergence] * len(jobs))
+        desc += f"; with the Eq. 4 convergence test (threshold {args.convergence:g})"
     out = plan.empty()
     stream = torch.cuda.current_stream()
 
@@ -246,11 +252,19 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_ms = float(t.item())
     ms_per_step = max_ms / args.steps
+    conv = None
+    if args.convergence is not None:
+        import numpy as np
+        # throughput counts the iterations the curves actually ran
+        d, run = plan.convergence()
+        sample_iters = sum((1 << int(j["log2n"])) * int(r) for j, r in zip(jobs, run))
+        conv = {"threshold": args.convergence, "mean_iters_run": float(np.mean(run)),
+                "median_last_delta": float(np.median([d[c, int(r) - 1] for c, r in enumerate(run) if r > 0]))}
     value = world * sample_iters * args.steps / (max_ms / 1000.0)
 
     # end-to-end through the host entry point: job table in, series out
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.convergence is None:
         host = torch.empty(samples, dtype=plan.dtype).pin_memory()
         jb = _abi.job_array(jobs)
         h2d = len(jobs) * _abi.ctypes.sizeof(_abi.LcJob)
@@ -299,6 +313,8 @@ def run_gpu(args):
                            "parallelism": f"curves sharded over {world} GPU(s), no collective"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}
+        if conv is not None:
+            line["convergence"] = conv
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

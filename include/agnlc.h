@@ -168,6 +168,40 @@ LC_API lc_status lc_plan_last_launches(lc_plan plan, uint64_t* launches);
  * A stage that did not run reports 0. */
 LC_API lc_status lc_plan_timing(lc_plan plan, float* setup_ms, float* iterate_ms);
 
+/* ------------------------------------------------------------ convergence */
+
+/* Turn on the convergence test of Sec. 3.2.2 (Eq. 4) for the plan's later
+ * lc_generate / lc_generate_host / lc_iterate runs.  After each iteration i
+ * (1-based) every running curve computes
+ *     delta_i = rms_n [ log10( x_i(t_n) / x_{i-1}(t_n) ) ],  n = 1..N,
+ * the root mean square about zero of the base-10 log ratio between its
+ * consecutive iterates (x_0 = the state the run starts from, after lc_setup
+ * the draws in draw order), records it, and stops when delta_i is strictly
+ * below its threshold: its remaining iterations of that run are skipped and
+ * its series stays x_i.  The record is reset at the start of every run.
+ *   thresholds: host array of ncurves doubles (job order), read during the
+ *               call; NULL = all 0.  A threshold <= 0 never stops its curve
+ *               (delta >= 0); +inf stops it after one iteration; NaN is
+ *               LC_ERR_INVALID.
+ *   history:    1..65536 iterations recorded per curve; later iterations
+ *               are still measured and can still stop the curve.
+ * The values must be positive (they are for every ERDF); with LC_FP32 a job
+ * with log_lmin < -37 is LC_ERR_INVALID (draws below FLT_MIN).  Allocates
+ * about ncurves * (history + 2) doubles plus one double per sort tile
+ * (owned by the plan) and blocks until done.  Calling it again replaces the
+ * thresholds.  Cost per iteration: one extra coalesced pass over the state
+ * (the fused kernels write each iterate back to the plan's state buffer; the
+ * multi-kernel path reads x_{i-1} and x_i and moves x_i into place). */
+LC_API lc_status lc_plan_set_convergence(lc_plan plan, const double* thresholds, uint32_t history);
+
+/* Record of the plan's last run (blocks until the plan's queued work is
+ * done).  deltas: host array of ncurves * history doubles or NULL; row c
+ * holds delta_1 .. delta_history of curve c, NaN for iterations it did not
+ * run.  iters_run: host array of ncurves uint32 or NULL: the iterations each
+ * curve ran (its job count, or fewer when it stopped).  LC_ERR_INVALID
+ * before lc_plan_set_convergence. */
+LC_API lc_status lc_plan_convergence(lc_plan plan, double* deltas, uint32_t* iters_run);
+
 /* Release the plan and its device memory (synchronises its stream). */
 LC_API lc_status lc_plan_destroy(lc_plan plan);
 

@@ -10,13 +10,15 @@ from __future__ import annotations
 
 from . import _abi
 from ._abi import (LC_FP32, LC_FP64, LcError, lc_generate, lc_generate_host, lc_get_state, lc_iterate,
-                   lc_plan_buffer, lc_plan_create, lc_plan_destroy, lc_plan_last_launches, lc_plan_timing,
-                   lc_plan_total_samples, lc_plan_workspace_bytes, lc_poll, lc_server_create,
-                   lc_server_destroy, lc_server_stats, lc_set_state, lc_setup, lc_submit)
+                   lc_plan_buffer, lc_plan_convergence, lc_plan_create, lc_plan_destroy, lc_plan_last_launches,
+                   lc_plan_set_convergence, lc_plan_timing, lc_plan_total_samples, lc_plan_workspace_bytes,
+                   lc_poll, lc_server_create, lc_server_destroy, lc_server_stats, lc_set_state, lc_setup,
+                   lc_submit)
 
 __all__ = ["Plan", "LC_FP32", "LC_FP64", "LcError", "lc_plan_create", "lc_generate", "lc_generate_host",
            "lc_setup", "lc_iterate", "lc_get_state", "lc_set_state", "lc_plan_buffer",
            "lc_plan_last_launches", "lc_plan_timing", "lc_plan_total_samples", "lc_plan_workspace_bytes", "lc_plan_destroy",
+           "lc_plan_set_convergence", "lc_plan_convergence",
            "lc_server_create", "lc_submit", "lc_poll", "lc_server_stats", "lc_server_destroy"]
 
 
@@ -74,6 +76,17 @@ class Plan:
 
         torch.cuda.current_stream(self.device).synchronize()
         return torch.as_tensor(_View(), device=f"cuda:{self.device}").clone()
+
+    def set_convergence(self, thresholds=None, history=None):
+        """Turn on the Sec. 3.2.2 convergence test (Eq. 4) with per-curve
+        thresholds (None: never stop); history defaults to the largest job count."""
+        h = int(history) if history is not None else max(1, max(int(j["iters"]) for j in self.jobs))
+        lc_plan_set_convergence(self.handle, thresholds, h)
+        self.history = h
+
+    def convergence(self):
+        """(deltas [ncurves, history], iters_run [ncurves]) of the last run."""
+        return lc_plan_convergence(self.handle, len(self.jobs), self.history)
 
     def curve(self, x, c):
         return x[self.offsets[c]:self.offsets[c + 1]]

@@ -58,6 +58,8 @@ _SIGS = {
     "lc_plan_buffer": (c_i32, [c_p, c_i32, ctypes.POINTER(c_p), ctypes.POINTER(c_sz)]),
     "lc_plan_last_launches": (c_i32, [c_p, ctypes.POINTER(c_u64)]),
     "lc_plan_timing": (c_i32, [c_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "lc_plan_set_convergence": (c_i32, [c_p, c_p, c_u32]),
+    "lc_plan_convergence": (c_i32, [c_p, c_p, c_p]),
     "lc_plan_destroy": (c_i32, [c_p]),
     "lc_generate_noalloc": (c_i32, [ctypes.POINTER(LcJob), c_p, c_p]),
     "lc_server_create": (c_i32, [c_i32, c_sz, c_i32, ctypes.POINTER(c_p)]),
@@ -207,6 +209,25 @@ def lc_plan_timing(plan):
     a, b = ctypes.c_float(), ctypes.c_float()
     _check(load().lc_plan_timing(plan, ctypes.byref(a), ctypes.byref(b)), "lc_plan_timing")
     return a.value, b.value
+
+
+def lc_plan_set_convergence(plan, thresholds, history):
+    """thresholds: None or a sequence of ncurves floats (host)."""
+    import numpy as np
+    if thresholds is None:
+        _check(load().lc_plan_set_convergence(plan, None, int(history)), "lc_plan_set_convergence")
+        return
+    t = np.ascontiguousarray(thresholds, dtype=np.float64)
+    _check(load().lc_plan_set_convergence(plan, t.ctypes.data_as(c_p), int(history)), "lc_plan_set_convergence")
+
+
+def lc_plan_convergence(plan, ncurves, history):
+    """(deltas [ncurves, history] float64, iters_run [ncurves] uint32) of the last run."""
+    import numpy as np
+    d = np.empty((ncurves, history), dtype=np.float64)
+    r = np.empty(ncurves, dtype=np.uint32)
+    _check(load().lc_plan_convergence(plan, d.ctypes.data_as(c_p), r.ctypes.data_as(c_p)), "lc_plan_convergence")
+    return d, r
 
 
 def lc_plan_destroy(plan):

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 
@@ -292,12 +293,25 @@ static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches)
 {
     for (auto& k : p.classes) {
         if (k.resident) continue;
-        void* R1 = launch_fft<T>(p, k, false, p.d_x, p.d_f, nullptr, true, st, launches);
-        void* Zp = (R1 == p.d_x) ? p.d_f : p.d_x;
+        // with the convergence test the FFTs work in d_f and d_keysB (free
+        // until the sort starts) so that x_{i-1} stays in d_x for Eq. 4
+        void* alt = p.conv_on ? p.d_keysB : p.d_x;
+        void* R1 = launch_fft<T>(p, k, false, p.d_x, p.d_f, nullptr, true, st, launches,
+                                 p.conv_on ? p.d_keysB : nullptr);
+        void* Zp = (R1 == p.d_f) ? alt : p.d_f;
         launch_spectral_iter<T>(p, k, R1, Zp, st);
         ++*launches;
         void* R3 = launch_fft<T>(p, k, true, Zp, R1, nullptr, true, st, launches);
-        launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches);
+        if (!p.conv_on) {
+            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches);
+        } else {
+            // the last sort pass reads keys A, so x_i can go to keys B; Eq. 4
+            // then compares it with x_{i-1} in one coalesced pass
+            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, p.d_keysB);
+            launch_conv_delta<T>(p, k, p.d_keysB, st);
+            launch_conv_finalize(p, k, st);
+            *launches += 2;
+        }
     }
     launch_iter_increment(p, st);
     ++*launches;
@@ -315,6 +329,10 @@ static lc_status run_iterations_impl(Plan& p, uint32_t override_iters, uint32_t 
     if (reset) {
         launch_eff_iters(p, override_iters, st);
         ++*launches;
+        if (p.conv_on) {
+            launch_conv_reset(p, st);
+            ++*launches;
+        }
     }
     // curves of the fused on-chip classes run all n_it iterations in one launch
     for (auto& k : p.classes)
@@ -372,6 +390,7 @@ void plan_free(Plan* p)
         cudaStreamSynchronize(p->stream);
         if (p->iter_graph) cudaGraphExecDestroy(p->iter_graph);
         cudaFree(p->arena);
+        if (p->conv_arena) cudaFree(p->conv_arena);
         if (p->d_tk_stage) cudaFree(p->d_tk_stage);
         cudaEventDestroy(p->ev_in);
         cudaEventDestroy(p->ev_out);
@@ -580,6 +599,82 @@ lc_status lc_plan_timing(lc_plan plan, float* setup_ms, float* iterate_ms)
     }
     if (setup_ms) *setup_ms = a;
     if (iterate_ms) *iterate_ms = b;
+    return LC_OK;
+}
+
+lc_status lc_plan_set_convergence(lc_plan plan, const double* thresholds, uint32_t history)
+{
+    if (!plan) { set_error("null plan"); return LC_ERR_INVALID; }
+    if (history < 1 || history > (1u << 16)) { set_error("history must be in [1, 65536]"); return LC_ERR_INVALID; }
+    const size_t nc = plan->ncurves;
+    std::vector<double> thr(nc, 0.0);
+    for (size_t c = 0; c < nc; ++c) {
+        if (thresholds) {
+            if (std::isnan(thresholds[c])) { set_error("threshold " + std::to_string(c) + " is NaN"); return LC_ERR_INVALID; }
+            thr[c] = thresholds[c];
+        }
+        // Eq. 4 takes logs of the values: float draws must stay normal numbers
+        if (plan->prec == LC_FP32 && plan->jobs[c].erdf.log_lmin < -37.0) {
+            set_error("job " + std::to_string(c) + ": log_lmin below -37 gives FP32 values below FLT_MIN");
+            return LC_ERR_INVALID;
+        }
+    }
+    DeviceGuard g(plan->device);
+    LC_CK(cudaStreamSynchronize(plan->stream));
+    size_t part = 0;
+    for (auto& k : plan->classes) {
+        const int C = k.resident && k.log2n > 14 ? 1 << (k.log2n - 14) : 0;
+        part = std::max(part, (size_t)k.ncurves * (size_t)std::max(k.tiles_per_curve, C));
+    }
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_thr = up(nc * 8), b_delta = up(nc * (size_t)history * 8), b_part = up(part * 8);
+    if (plan->conv_arena && (plan->conv.hist != history || plan->conv_part != part)) {
+        cudaFree(plan->conv_arena);
+        plan->conv_arena = nullptr;
+    }
+    if (!plan->conv_arena) {
+        if (cudaMalloc(&plan->conv_arena, b_thr + b_delta + b_part) != cudaSuccess) {
+            cudaGetLastError();
+            plan->conv_on = false;
+            set_error("device allocation of the convergence record failed");
+            return LC_ERR_NOMEM;
+        }
+    }
+    char* b = (char*)plan->conv_arena;
+    plan->conv.thr = (const double*)b;
+    plan->conv.delta = (double*)(b + b_thr);
+    plan->conv.part = (double*)(b + b_thr + b_delta);
+    plan->conv.hist = history;
+    plan->conv_part = part;
+    plan->conv_on = true;
+    LC_CK(cudaMemcpyAsync((void*)plan->conv.thr, thr.data(), nc * 8, cudaMemcpyHostToDevice, plan->stream));
+    launch_conv_reset(*plan, plan->stream);
+    LC_CK(cudaStreamSynchronize(plan->stream));
+    // the captured iteration graph has the kernels of the other mode
+    if (plan->iter_graph) {
+        cudaGraphExecDestroy(plan->iter_graph);
+        plan->iter_graph = nullptr;
+    }
+    return LC_OK;
+}
+
+lc_status lc_plan_convergence(lc_plan plan, double* deltas, uint32_t* iters_run)
+{
+    if (!plan) { set_error("null plan"); return LC_ERR_INVALID; }
+    if (!plan->conv_on) { set_error("lc_plan_convergence before lc_plan_set_convergence"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    LC_CK(cudaStreamSynchronize(plan->stream));
+    const size_t nc = plan->ncurves;
+    std::vector<uint32_t> eff(nc);
+    int it = 0;
+    if (deltas)
+        LC_CK(cudaMemcpyAsync(deltas, plan->conv.delta, nc * (size_t)plan->conv.hist * 8, cudaMemcpyDeviceToHost,
+                              plan->stream));
+    LC_CK(cudaMemcpyAsync(eff.data(), plan->d_eff_iters, nc * 4, cudaMemcpyDeviceToHost, plan->stream));
+    LC_CK(cudaMemcpyAsync(&it, plan->d_iter, sizeof(int), cudaMemcpyDeviceToHost, plan->stream));
+    LC_CK(cudaStreamSynchronize(plan->stream));
+    if (iters_run)
+        for (size_t c = 0; c < nc; ++c) iters_run[c] = std::min(eff[c], (uint32_t)std::max(it, 0));
     return LC_OK;
 }
 

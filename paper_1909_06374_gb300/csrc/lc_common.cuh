@@ -267,4 +267,58 @@ __device__ __forceinline__ double erdf_draw(const ErdfConst& k, double U)
     return lam;
 }
 
+// ----------------------------------------------------------- convergence
+// Convergence test of Sec. 3.2.2 (Eq. 4): delta_i = rms_n log10(x_i/x_{i-1}).
+struct ConvDev {
+    const double* thr;   // [ncurves] stop thresholds (delta_i < thr stops the curve)
+    double* delta;       // [ncurves][hist] delta of 0-based iteration i (NaN: not run)
+    double* part;        // per-block partial sums of squared natural-log ratios
+    uint32_t hist;       // iterations recorded per curve
+};
+
+// (ln(xn/xp))^2 for positive xn, xp.  Near 1 the ratio is taken as
+// log1p((xn - xp)/xp): the difference is exact there (the two are within a
+// factor two), so a small change keeps its relative accuracy.  Far from 1 the
+// quotient is used, or the difference of logs when it would leave the normal
+// range.
+__device__ __forceinline__ float ln_ratio_sq(float xn, float xp)
+{
+    const float d = xn - xp;
+    float t;
+    if (fabsf(d) <= 0.5f * xp) {
+        t = log1pf(__fdiv_rn(d, xp));
+    } else {
+        const float r = __fdiv_rn(xn, xp);
+        t = (r >= 1.17549435e-38f && r <= 3.40282347e+38f) ? logf(r) : logf(xn) - logf(xp);
+    }
+    return t * t;
+}
+__device__ __forceinline__ double ln_ratio_sq(double xn, double xp)
+{
+    const double d = xn - xp;
+    double t;
+    if (fabs(d) <= 0.5 * xp) {
+        t = log1p(__ddiv_rn(d, xp));
+    } else {
+        const double r = __ddiv_rn(xn, xp);
+        t = (r >= 2.2250738585072014e-308 && r <= 1.7976931348623157e+308) ? log(r) : log(xn) - log(xp);
+    }
+    return t * t;
+}
+
+// delta from the sum of (ln ratio)^2 over the n samples of a curve
+// (log10 = ln / ln 10).
+__device__ __forceinline__ double conv_delta(double sum_ln2, double n)
+{
+    return sqrt(sum_ln2 / n) * 0.43429448190325182765;
+}
+
+// Records delta of iteration i for curve c (caller: one thread) and returns
+// whether the curve stops after it.
+__device__ __forceinline__ bool conv_record(const ConvDev& cv, int c, int i, double delta)
+{
+    if ((uint32_t)i < cv.hist) cv.delta[(size_t)c * cv.hist + i] = delta;
+    return delta < cv.thr[c];
+}
+
 }  // namespace lc

@@ -418,7 +418,7 @@ static void launch_tile(int LR, const PassArgs& a, int blocks, cudaStream_t st)
 
 template <typename T>
 void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void* other, void* final_out,
-                 bool gated, cudaStream_t st, uint64_t* launches)
+                 bool gated, cudaStream_t st, uint64_t* launches, void* scratch)
 {
     if (k.log2n - 1 >= 12) {
         PassArgs a;
@@ -443,7 +443,7 @@ void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void
             if (launches) ++*launches;
             log2p += (uint32_t)lr[q];
             void* written = a.out;
-            nxt = cur;
+            nxt = (q == 0 && scratch) ? scratch : cur;
             cur = written;
         }
         return cur;
@@ -471,7 +471,7 @@ void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void
         if (launches) ++*launches;
         log2p += (uint32_t)ilog2c(R);
         void* written = a.out;
-        nxt = cur;
+        nxt = (q == 0 && scratch) ? scratch : cur;
         cur = written;
     }
     return cur;
@@ -499,8 +499,10 @@ void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_
 
 template void launch_twiddles<float>(const ClassInfo&, cudaStream_t);
 template void launch_twiddles<double>(const ClassInfo&, cudaStream_t);
-template void* launch_fft<float>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*);
-template void* launch_fft<double>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*);
+template void* launch_fft<float>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*,
+                                 void*);
+template void* launch_fft<double>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*,
+                                  void*);
 template void launch_spectral_iter<float>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
 template void launch_spectral_iter<double>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
 template void launch_spectral_tk<float>(const Plan&, const ClassInfo&, void*, cudaStream_t);

@@ -75,7 +75,16 @@ struct Plan {
     uint64_t last_launches = 0;
     bool setup_done = false;
     int path_mode = 0;        // 0 auto (measured table), 1 resident where possible, 2 multi-kernel
+
+    // convergence test (Sec. 3.2.2, Eq. 4), off until lc_plan_set_convergence
+    bool conv_on = false;
+    void* conv_arena = nullptr;  // thresholds, delta record, partial sums
+    ConvDev conv{};
+    size_t conv_part = 0;        // doubles in conv.part
 };
+
+// ConvDev of a plan: null pointers when the convergence test is off.
+inline ConvDev conv_of(const Plan& p) { return p.conv_on ? p.conv : ConvDev{}; }
 
 // setup stage (lc_setup.cu)
 int spec_blocks_per_curve(uint32_t log2n);
@@ -90,10 +99,12 @@ template <typename T> void launch_twiddles(const ClassInfo& k, cudaStream_t st);
 // Complex FFT of every curve of the class (forward: e^{-}, inverse: e^{+}),
 // ping-ponging between `in` and `other`; the last pass writes `final_out`
 // when it is non-null.  Returns the buffer that holds the result.  When
-// `gated` the kernels skip curves whose iteration budget is spent.
+// `gated` the kernels skip curves whose iteration budget is spent.  A
+// non-null `scratch` takes the place of `in` after the first pass, so that
+// `in` is only read.
 template <typename T> void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in,
                                        void* other, void* final_out, bool gated, cudaStream_t st,
-                                       uint64_t* launches);
+                                       uint64_t* launches, void* scratch = nullptr);
 template <typename T> void launch_spectral_iter(const Plan& p, const ClassInfo& k, const void* Z,
                                                 void* Zp, cudaStream_t st);
 template <typename T> void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_t st);
@@ -103,10 +114,14 @@ constexpr int kSortTile = 2048;
 constexpr int kScanChunk = 32;
 enum SortMode { kSortArgsortScatter = 1, kSortKeysToValues = 2 };
 // Stable LSD radix sort of each curve's values `src` (order keys of T):
-// kSortArgsortScatter writes x[perm[r]] = s[r]; kSortKeysToValues writes the
-// sorted values to s.
+// kSortArgsortScatter writes x[perm[r]] = s[r] (x = x_out, default the
+// state); kSortKeysToValues writes the sorted values to s.
 template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode,
-                                       bool gated, cudaStream_t st, uint64_t* launches);
+                                       bool gated, cudaStream_t st, uint64_t* launches, void* x_out = nullptr);
+// Eq. 4 partial sums of a multi-kernel class between the state x_{i-1} and
+// the new iterate x_i in `xnew` (one double per sort tile, curve-major, in
+// conv.part), moving x_i into the state; for launch_conv_finalize.
+template <typename T> void launch_conv_delta(const Plan& p, const ClassInfo& k, const void* xnew, cudaStream_t st);
 
 // fused on-chip iteration (lc_resident.cu)
 bool resident_supported(const Plan& p, uint32_t log2n);
@@ -117,6 +132,12 @@ size_t resident_exchange_floats(uint32_t log2n);
 // Runs n_it iterations (from the plan's current iteration index) of every
 // curve of a resident class in one launch.
 void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStream_t st, uint64_t* launches);
+
+// Eq. 4 per curve of a multi-kernel class from the tile partial sums of the
+// last scatter; records delta and stops the curves that fell below threshold.
+void launch_conv_finalize(const Plan& p, const ClassInfo& k, cudaStream_t st);
+// Marks the whole delta record "not run" (NaN).
+void launch_conv_reset(const Plan& p, cudaStream_t st);
 
 void launch_iter_increment(const Plan& p, cudaStream_t st);
 void launch_iter_add(const Plan& p, uint32_t n, cudaStream_t st);

@@ -211,7 +211,7 @@ __device__ __forceinline__ uint32_t scan256(uint32_t v, uint32_t* wsum)
 struct ResArgs {
     const int* cls_curves;
     const CurveDev* curves;
-    const uint32_t* eff_iters;
+    uint32_t* eff_iters;  // lowered when the convergence test stops a curve
     const int* d_iter;
     const float* A;
     const float* s;
@@ -220,7 +220,24 @@ struct ResArgs {
     float* rx;           // cluster exchange area: 3 N floats per curve of the class
     uint32_t n_it;
     uint32_t log2n;
+    ConvDev conv;        // convergence test (Sec. 3.2.2, Eq. 4); conv.delta null: off
 };
+
+// Sum of one float per thread of the CTA in FP64, in a fixed order (warp
+// tree, then warps in order); every thread gets the result.  red: kResWarps
+// doubles of shared memory.
+__device__ __forceinline__ double cta_sum(float v, double* red)
+{
+    double d = (double)v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kResWarps; ++w) t += red[w];
+    return t;
+}
 
 // One stable LSD radix pass over the L = 2^LOG2L keys of the CTA (warp w
 // owns elements [w L/16, (w+1) L/16), lane-striped).  FIRST: keys are the
@@ -303,7 +320,7 @@ __device__ __forceinline__ void radix_pass(const float* __restrict__ xa, const u
 }
 
 // ------------------------------------------------------------- one CTA
-template <int LOG2L>
+template <int LOG2L, bool CONV>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident_cta(const ResArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -319,6 +336,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_cta(const ResArgs a
     float2* twhi = twlo + kTwLo;
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wsum[8];
+    __shared__ double red[kResWarps];
 
     const int c = a.cls_curves[blockIdx.x];
     const CurveDev& cv = a.curves[c];
@@ -354,6 +372,37 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_cta(const ResArgs a
         radix_pass<LOG2L, false, true>(nullptr, kO, nullptr, ia, nullptr, (float*)X, s, 24, wh, dbase, wsum);
         z = X;
         o = other;
+        if (CONV) {
+            // Eq. 4 against the previous iterate, which the state in global
+            // memory holds in this mode (it is rewritten every iteration)
+            __syncthreads();
+            const float* Xf = (const float*)X;
+            float lsum = 0.0f;
+            constexpr int PER = (1 << LOG2L) / kResThreads;  // 2 .. 32 samples per thread
+            constexpr int G = PER < 8 ? PER : 8;              // loads issued before stores
+#pragma unroll
+            for (int g0 = 0; g0 < PER; g0 += G) {
+                float xn[G], xo[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    const int m = threadIdx.x + (g0 + j) * kResThreads;
+                    xo[j] = xg[m];
+                    xn[j] = Xf[fsw(m)];
+                }
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    lsum += ln_ratio_sq(xn[j], xo[j]);
+                    xg[threadIdx.x + (g0 + j) * kResThreads] = xn[j];
+                }
+            }
+            const double delta = conv_delta(cta_sum(lsum, red), (double)L);
+            const bool stop = delta < a.conv.thr[c];
+            if (threadIdx.x == 0) {
+                conv_record(a.conv, c, it0 + it, delta);
+                if (stop) a.eff_iters[c] = (uint32_t)(it0 + it + 1);
+            }
+            if (stop) break;
+        }
     }
     float2* xo2 = (float2*)xg;
     for (int m = threadIdx.x; m < M; m += kResThreads) xo2[m] = z[swz(m)];
@@ -383,7 +432,7 @@ __device__ __forceinline__ int advance_count(const uint32_t* sorted, int n, int 
     return lo;
 }
 
-template <int C>
+template <int C, bool CONV>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kResThreads, 1) k_resident_cluster(const ResArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -404,6 +453,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kResThreads, 1) k_re
     float2* twhi = twlo + kTwLo;
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wsum[8];
+    __shared__ double red[kResWarps];
 
     const int ci = blockIdx.x / C;
     const int c = a.cls_curves[ci];
@@ -517,23 +567,88 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kResThreads, 1) k_re
             }
             __syncthreads();
         }
-        // rank-order replacement straight into the state in L2
+        // rank-order replacement straight into the state in L2 (with the
+        // convergence test, the old value there enters Eq. 4 first)
+        constexpr bool conv = CONV;
+        float lsum = 0.0f;
+        if (!conv) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            if (e < per) {
-                const int p = threadIdx.x * per + e;
-                __stcg(xs + me * L + ib[p], __ldg(s + ((gr[e >> 1] >> ((e & 1) * 16)) & 0xffffu)));
+            for (int e = 0; e < 32; ++e) {
+                if (e < per) {
+                    const int p = threadIdx.x * per + e;
+                    __stcg(xs + me * L + ib[p], __ldg(s + ((gr[e >> 1] >> ((e & 1) * 16)) & 0xffffu)));
+                }
+            }
+        } else {
+            // groups of 8: the old values' loads are issued before the stores
+#pragma unroll
+            for (int e0 = 0; e0 < 32; e0 += 8) {
+                if (e0 < per) {
+                    float xn[8], xo[8];
+#pragma unroll
+                    for (int e = e0; e < e0 + 8; ++e) {
+                        const int p = threadIdx.x * per + e;
+                        xn[e - e0] = __ldg(s + ((gr[e >> 1] >> ((e & 1) * 16)) & 0xffffu));
+                        xo[e - e0] = __ldcg(xs + me * L + ib[p]);
+                    }
+#pragma unroll
+                    for (int e = e0; e < e0 + 8; ++e) {
+                        const int p = threadIdx.x * per + e;
+                        lsum += ln_ratio_sq(xn[e - e0], xo[e - e0]);
+                        __stcg(xs + me * L + ib[p], xn[e - e0]);
+                    }
+                }
             }
         }
-        cl.sync();  // the next state is complete
+        if (conv) {
+            const double part = cta_sum(lsum, red);
+            if (threadIdx.x == 0) __stcg(a.conv.part + (size_t)ci * C + me, part);
+        }
+        cl.sync();  // the next state (and every CTA's partial sum) is complete
+        if (conv) {
+            // every CTA sums the C partials in the same order, so all take the
+            // same decision; a partial is rewritten only after the next
+            // iteration's first cluster barrier, when all have read it
+            double sum = 0.0;
+#pragma unroll
+            for (int q = 0; q < C; ++q) sum += __ldcg(a.conv.part + (size_t)ci * C + q);
+            const double delta = conv_delta(sum, (double)N);
+            const bool stop = delta < a.conv.thr[c];
+            if (me == 0 && threadIdx.x == 0) {
+                conv_record(a.conv, c, it0 + it, delta);
+                if (stop) a.eff_iters[c] = (uint32_t)(it0 + it + 1);
+            }
+            if (stop) break;
+        }
     }
+}
+
+template <int LOG2L, bool CONV>
+void launch_cta_mode(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
+{
+    cudaFuncSetAttribute(k_resident_cta<LOG2L, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    k_resident_cta<LOG2L, CONV><<<ncurves, kResThreads, smem, st>>>(a);
 }
 
 template <int LOG2L>
 void launch_cta(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
 {
-    cudaFuncSetAttribute(k_resident_cta<LOG2L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    k_resident_cta<LOG2L><<<ncurves, kResThreads, smem, st>>>(a);
+    if (a.conv.delta) launch_cta_mode<LOG2L, true>(a, ncurves, smem, smax, st);
+    else launch_cta_mode<LOG2L, false>(a, ncurves, smem, smax, st);
+}
+
+template <int C, bool CONV>
+void launch_cluster_mode(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
+{
+    cudaFuncSetAttribute(k_resident_cluster<C, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    k_resident_cluster<C, CONV><<<ncurves * C, kResThreads, smem, st>>>(a);
+}
+
+template <int C>
+void launch_cluster(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
+{
+    if (a.conv.delta) launch_cluster_mode<C, true>(a, ncurves, smem, smax, st);
+    else launch_cluster_mode<C, false>(a, ncurves, smem, smax, st);
 }
 
 }  // namespace
@@ -568,6 +683,7 @@ void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStrea
     a.rx = k.d_rx;
     a.n_it = n_it;
     a.log2n = k.log2n;
+    a.conv = conv_of(p);
     const int C = k.log2n <= kResMaxLog2 ? 1 : 1 << (k.log2n - kResMaxLog2);
     const size_t L = ((size_t)1 << k.log2n) / C;
     const size_t smem = 12 * L + kWhBytes + kTwBytes;
@@ -581,11 +697,9 @@ void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStrea
         default: launch_cta<14>(a, k.ncurves, smem, smax, st); break;
         }
     } else if (C == 2) {
-        cudaFuncSetAttribute(k_resident_cluster<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-        k_resident_cluster<2><<<k.ncurves * 2, kResThreads, smem, st>>>(a);
+        launch_cluster<2>(a, k.ncurves, smem, smax, st);
     } else {
-        cudaFuncSetAttribute(k_resident_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-        k_resident_cluster<4><<<k.ncurves * 4, kResThreads, smem, st>>>(a);
+        launch_cluster<4>(a, k.ncurves, smem, smax, st);
     }
     if (launches) ++*launches;
 }

@@ -10,6 +10,8 @@
 // per-warp counts) and writes each digit's run with coalesced stores.  The
 // last pass of an argsort writes x[k] = s[rank] directly instead of the
 // sorted pairs.
+#include <algorithm>
+
 #include "lc_internal.h"
 
 namespace lc {
@@ -229,19 +231,136 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
         }
     }
     __syncthreads();
-    for (int i = tid; i < tl; i += kSortThreads) {
-        const K k = sk[i];
-        const uint32_t d = (uint32_t)(k >> a.shift) & 255u;
-        const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
-        if (MODE == 0) {
-            ((K*)a.keys_out)[off + dest] = k;
-            a.vals_out[off + dest] = sv[i];
-        } else if (MODE == kSortArgsortScatter) {
-            ((T*)a.x_out)[off + sv[i]] = ((const T*)a.s_in)[off + dest];
-        } else {
-            ((T*)a.s_out)[off + dest] = key_value(k);
+    if (MODE == kSortArgsortScatter) {
+        // every run read of s is issued before the thread's first store, so
+        // the loads overlap instead of waiting behind possibly aliasing stores
+        T xn[kSlots];
+        uint32_t pos[kSlots];
+#pragma unroll
+        for (int e = 0; e < kSlots; ++e) {
+            const int i = tid + e * kSortThreads;
+            if (i < tl) {
+                const K k = sk[i];
+                const uint32_t d = (uint32_t)(k >> a.shift) & 255u;
+                const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
+                pos[e] = sv[i];
+                xn[e] = ((const T*)a.s_in)[off + dest];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < kSlots; ++e)
+            if (tid + e * kSortThreads < tl) ((T*)a.x_out)[off + pos[e]] = xn[e];
+    } else {
+        for (int i = tid; i < tl; i += kSortThreads) {
+            const K k = sk[i];
+            const uint32_t d = (uint32_t)(k >> a.shift) & 255u;
+            const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
+            if (MODE == 0) {
+                ((K*)a.keys_out)[off + dest] = k;
+                a.vals_out[off + dest] = sv[i];
+            } else {
+                ((T*)a.s_out)[off + dest] = key_value(k);
+            }
         }
     }
+}
+
+// Eq. 4 (Sec. 3.2.2) from the two iterates, both in natural order: one tile
+// of a curve per block reads x_{i-1} (x) and x_i (xnew, where the last sort
+// pass left it), adds up (ln x_i/x_{i-1})^2 in a fixed order and moves x_i
+// into x.  12 B per sample (FP32), coalesced.
+template <typename T>
+__global__ void __launch_bounds__(kSortThreads) k_conv_delta(const int* __restrict__ cls_curves,
+                                                             const CurveDev* __restrict__ curves, int tpc,
+                                                             int tile_len, const uint32_t* __restrict__ eff_iters,
+                                                             const int* __restrict__ d_iter,
+                                                             const T* __restrict__ xnew, T* __restrict__ x,
+                                                             double* __restrict__ part)
+{
+    const int ci = blockIdx.x / tpc;
+    const int t = blockIdx.x % tpc;
+    const int c = cls_curves[ci];
+    if ((uint32_t)*d_iter >= eff_iters[c]) return;
+    const uint64_t base = curves[c].off + (uint64_t)t * tile_len;
+    const int tid = threadIdx.x;
+    T lsum = 0;
+    T xn[kSlots], xo[kSlots];
+#pragma unroll
+    for (int e = 0; e < kSlots; ++e) {
+        const int i = tid + e * kSortThreads;
+        if (i < tile_len) {
+            xn[e] = xnew[base + i];
+            xo[e] = x[base + i];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kSlots; ++e) {
+        const int i = tid + e * kSortThreads;
+        if (i < tile_len) {
+            lsum += ln_ratio_sq(xn[e], xo[e]);
+            x[base + i] = xn[e];
+        }
+    }
+    // tile sum in a fixed order: warp tree, then the warps in order
+    double v = (double)lsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ double wpart[kSortWarps];
+    if ((tid & 31) == 0) wpart[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double tsum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) tsum += wpart[w];
+        part[blockIdx.x] = tsum;
+    }
+}
+
+template <typename T>
+void launch_conv_delta(const Plan& p, const ClassInfo& k, const void* xnew, cudaStream_t st)
+{
+    k_conv_delta<T><<<k.ncurves * k.tiles_per_curve, kSortThreads, 0, st>>>(
+        k.d_curves, p.d_curves, k.tiles_per_curve, k.tile_len, p.d_eff_iters, p.d_iter, (const T*)xnew,
+        (T*)p.d_x, p.conv.part);
+}
+template void launch_conv_delta<float>(const Plan&, const ClassInfo&, const void*, cudaStream_t);
+template void launch_conv_delta<double>(const Plan&, const ClassInfo&, const void*, cudaStream_t);
+
+// Eq. 4 per curve of the class: the tile sums of the last scatter in tile
+// order, delta = sqrt(sum / N) / ln 10; the curve stops after this iteration
+// when delta falls below its threshold.
+__global__ void k_conv_finalize(const int* __restrict__ cls_curves, const CurveDev* __restrict__ curves,
+                                int ncurves, int tpc, const int* __restrict__ d_iter,
+                                uint32_t* __restrict__ eff_iters, ConvDev cv)
+{
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= ncurves) return;
+    const int c = cls_curves[ci];
+    const int i = *d_iter;
+    if ((uint32_t)i >= eff_iters[c]) return;
+    double sum = 0.0;
+    for (int t = 0; t < tpc; ++t) sum += cv.part[(size_t)ci * tpc + t];
+    const double delta = conv_delta(sum, (double)(1ull << curves[c].log2n));
+    if (conv_record(cv, c, i, delta)) eff_iters[c] = (uint32_t)i + 1u;
+}
+
+__global__ void k_conv_reset(double* __restrict__ delta, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        delta[q] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+void launch_conv_finalize(const Plan& p, const ClassInfo& k, cudaStream_t st)
+{
+    k_conv_finalize<<<(k.ncurves + 127) / 128, 128, 0, st>>>(k.d_curves, p.d_curves, k.ncurves, k.tiles_per_curve,
+                                                             p.d_iter, p.d_eff_iters, p.conv);
+}
+
+void launch_conv_reset(const Plan& p, cudaStream_t st)
+{
+    const size_t n = p.ncurves * (size_t)p.conv.hist;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_conv_reset<<<blocks, 256, 0, st>>>(p.conv.delta, n);
 }
 
 template <typename T, bool FIRST>
@@ -254,7 +373,7 @@ static void launch_scatter(int mode, const SortArgs& a, int blocks, cudaStream_t
 
 template <typename T>
 void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode, bool gated,
-                 cudaStream_t st, uint64_t* launches)
+                 cudaStream_t st, uint64_t* launches, void* x_out)
 {
     using K = typename key_of<T>::type;
     const int passes = (int)sizeof(K);  // 8-bit digits
@@ -266,7 +385,7 @@ void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mo
     a.src = src;
     a.hist = p.d_hist + k.hist_off;
     a.cbase = p.d_cbase + k.cbase_off;
-    a.x_out = p.d_x;
+    a.x_out = x_out ? x_out : p.d_x;
     a.s_in = p.d_s;
     a.s_out = p.d_s;
     a.ncurves = k.ncurves;
@@ -293,7 +412,9 @@ void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mo
     }
 }
 
-template void launch_sort<float>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t, uint64_t*);
-template void launch_sort<double>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t, uint64_t*);
+template void launch_sort<float>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t, uint64_t*,
+                                void*);
+template void launch_sort<double>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t,
+                                 uint64_t*, void*);
 
 }  // namespace lc
