@@ -55,7 +55,10 @@ def lib():
                 "or_spec_log": (d, [d]),
                 "or_spec_log1p": (d, [d]),
                 "or_erdf_icdf": (d, [P, i32, d]),
-                "or_erdf_draws": (None, [P, i32, u64, u64, i32, sz, P]),
+                "or_erdf_draws": (None, [P, i32, i32, u64, u64, i32, sz, P]),
+                "or_erdf_density": (d, [P, i32, i32, d]),
+                "or_erdf_table": (None, [P, i32, i32, P]),
+                "or_erdf_icdf_tab": (d, [P, P, d]),
                 "or_psd": (d, [d, d, d, d]),
                 "or_tk_spectrum": (None, [u32, d, P, u64, u64, P]),
                 "or_dft": (None, [sz, P, P, i32]),
@@ -68,8 +71,8 @@ def lib():
                 "or_iterate": (None, [u32, P, P, P, u32, P, P]),
                 "or_delta": (d, [sz, P, P]),
                 "or_iterate_conv": (u32, [u32, P, P, P, u32, d, P]),
-                "or_generate": (None, [u32, P, i32, u32, u64, u64, i32, P, P, P, P]),
-                "or_generate_batch": (i32, [sz, P, P, P, P, P, P, i32, i32, P]),
+                "or_generate": (None, [u32, P, i32, i32, u32, u64, u64, i32, P, P, P, P]),
+                "or_generate_batch": (i32, [sz, P, P, P, P, P, P, P, i32, i32, P]),
                 "or_spec_exp_v": (None, [sz, P, P]),
                 "or_spec_log_v": (None, [sz, P, P]),
                 "or_spec_log1p_v": (None, [sz, P, P]),
@@ -127,9 +130,40 @@ def erdf_icdf(erdf, U, linear_space=0):
     lib().or_erdf_icdf_v(_p(e), int(linear_space), U.size, _p(U), _p(out)); return out
 
 
-def erdf_draws(erdf, n, seed, curve_id, prec=0, linear_space=0):
-    e = _f64(erdf); out = np.empty(n, dtype=np.float64)
-    lib().or_erdf_draws(_p(e), int(linear_space), seed, curve_id, prec, n, _p(out)); return out
+ERDF_TABLE = 4096  # intervals of the tabulated CDF (kinds 1, 2)
+
+
+def _erdf6(erdf, sigma=None):
+    """{log_lmin, log_lmax, log_lbreak, slope_low, slope_high, sigma}."""
+    e = list(np.asarray(erdf, dtype=np.float64).ravel())
+    if len(e) == 5:
+        e.append(0.0 if sigma is None else float(sigma))
+    elif sigma is not None:
+        e[5] = float(sigma)
+    return _f64(e)
+
+
+def erdf_draws(erdf, n, seed, curve_id, prec=0, linear_space=0, kind=0, sigma=None):
+    e = _erdf6(erdf, sigma); out = np.empty(n, dtype=np.float64)
+    lib().or_erdf_draws(_p(e), int(linear_space), int(kind), seed, curve_id, prec, n, _p(out)); return out
+
+
+def erdf_density(erdf, u, kind, linear_space=0, sigma=None):
+    """Unnormalised ERDF density in u = log10 lambda (kinds 0, 1, 2)."""
+    e = _erdf6(erdf, sigma)
+    return np.array([lib().or_erdf_density(_p(e), int(kind), int(linear_space), float(v))
+                     for v in np.atleast_1d(u)])
+
+
+def erdf_table(erdf, kind, linear_space=0, sigma=None):
+    """Unnormalised CDF at the ERDF_TABLE + 1 grid nodes."""
+    e = _erdf6(erdf, sigma); F = np.empty(ERDF_TABLE + 1)
+    lib().or_erdf_table(_p(e), int(kind), int(linear_space), _p(F)); return F
+
+
+def erdf_icdf_tab(erdf, F, U, sigma=None):
+    e = _erdf6(erdf, sigma); F = _f64(F)
+    return np.array([lib().or_erdf_icdf_tab(_p(e), _p(F), float(v)) for v in np.atleast_1d(U)])
 
 
 def psd(f, f_br, a_low, a_high):
@@ -207,10 +241,10 @@ def iterate_conv(A, s, x, iters, thr=0.0):
 
 
 def job_params(job) -> np.ndarray:
-    """Flatten a job dict into the oracle's 9-double parameter block."""
+    """Flatten a job dict into the oracle's 10-double parameter block."""
     return np.array([job["dt"], job["f_br"], job["alpha_low"], job["alpha_high"],
                      job["log_lmin"], job["log_lmax"], job["log_lbreak"],
-                     job["slope_low"], job["slope_high"]], dtype=np.float64)
+                     job["slope_low"], job["slope_high"], job.get("sigma", 0.0)], dtype=np.float64)
 
 
 def generate(job, prec=0, want=("x",)):
@@ -219,7 +253,8 @@ def generate(job, prec=0, want=("x",)):
     log2n = int(job["log2n"]); n = 1 << log2n
     par = job_params(job)
     out = {k: (np.empty(n // 2 + 1) if k == "A" else np.empty(n)) for k in ("x", "tk", "A", "s")}
-    lib().or_generate(log2n, _p(par), int(job.get("linear_space", 0)), int(job["iters"]),
+    lib().or_generate(log2n, _p(par), int(job.get("linear_space", 0)), int(job.get("erdf_kind", 0)),
+                      int(job["iters"]),
                       int(job["seed"]), int(job["curve_id"]), prec, _p(out["x"]),
                       _p(out["tk"]) if "tk" in want else None,
                       _p(out["A"]) if "A" in want else None,
@@ -233,11 +268,12 @@ def generate_batch(jobs, prec=0, nthreads=1):
     log2n = np.array([j["log2n"] for j in jobs], dtype=np.uint32)
     par = np.ascontiguousarray(np.stack([job_params(j) for j in jobs]))
     lin = np.array([j.get("linear_space", 0) for j in jobs], dtype=np.int32)
+    kind = np.array([j.get("erdf_kind", 0) for j in jobs], dtype=np.int32)
     iters = np.array([j["iters"] for j in jobs], dtype=np.uint32)
     seed = np.array([j["seed"] for j in jobs], dtype=np.uint64)
     cid = np.array([j["curve_id"] for j in jobs], dtype=np.uint64)
     total = int(sum(1 << int(l) for l in log2n))
     out = np.empty(total)
-    used = lib().or_generate_batch(nc, _p(log2n), _p(par), _p(lin), _p(iters), _p(seed),
+    used = lib().or_generate_batch(nc, _p(log2n), _p(par), _p(lin), _p(kind), _p(iters), _p(seed),
                                    _p(cid), prec, int(nthreads), _p(out))
     return out, int(used)

@@ -197,6 +197,9 @@ OR_API double or_spec_log1p(double y)
 /* clamped to [10^umin, 10^umax].                                            */
 /* erdf[] = {log_lmin, log_lmax, log_lbreak, slope_low, slope_high}.         */
 /* ------------------------------------------------------------------------ */
+/* Intervals of the tabulated ERDF CDF (kinds 1 and 2 below). */
+#define OR_ERDF_TABLE 4096
+
 OR_API double or_erdf_icdf(const double erdf[5], int linear_space, double U)
 {
     double umin = erdf[0], umax = erdf[1], ub = erdf[2];
@@ -240,19 +243,101 @@ OR_API double or_erdf_icdf(const double erdf[5], int linear_space, double U)
     return lam;
 }
 
+/* ------------------------------------------------------------------------ */
+/* ERDF shapes without a closed-form inverse CDF (Sec. 2.1.1):              */
+/*   kind 1, the smooth broken power law of Eq. 1:                          */
+/*     dN/du ~ [10^{-a1 (u-ub)} + 10^{-a2 (u-ub)}]^-1                       */
+/*     (Eq. 1's delta_1 = -a1, delta_2 = -a2, log lambda* = ub), which tends  */
+/*     to the sharp form's branches 10^{a1 (u-ub)} / 10^{a2 (u-ub)} away from */
+/*     the break;                                                           */
+/*   kind 2, the log-normal of Eq. 2: dN/du ~ exp(-(u-ub)^2 / (2 sigma^2))  */
+/*     (log lambda* = ub, sigma-tilde = sigma, in dex);                     */
+/*   kind 0, the sharp form, is also accepted here (used to check the        */
+/*     tabulated inversion against the closed form).                        */
+/* linear_space multiplies the density by 10^{u-ub} (dN/dlambda form).      */
+/* erdf[] = {log_lmin, log_lmax, log_lbreak, slope_low, slope_high, sigma}.  */
+/* ------------------------------------------------------------------------ */
+OR_API double or_erdf_density(const double erdf[6], int kind, int linear_space, double u)
+{
+    double ub = erdf[2], d = u - ub;
+    double a1 = erdf[3], a2 = erdf[4];
+    if (linear_space) { a1 = a1 + 1.0; a2 = a2 + 1.0; }
+    if (kind == 0) return d < 0.0 ? or_spec_exp(a1 * OR_LN10 * d) : or_spec_exp(a2 * OR_LN10 * d);
+    if (kind == 1) {
+        double c1 = a1 * OR_LN10, c2 = a2 * OR_LN10;
+        return 1.0 / (or_spec_exp(-c1 * d) + or_spec_exp(-c2 * d));
+    }
+    double t = d / erdf[5];
+    double e = -0.5 * t * t;
+    if (linear_space) e = e + OR_LN10 * d;
+    return or_spec_exp(e);
+}
+
+/* Unnormalised CDF on the uniform grid u_k = umin + k h, h = (umax-umin)/T, */
+/* T = OR_ERDF_TABLE: F_0 = 0, F_{k+1} = F_k + Simpson's rule on [u_k,      */
+/* u_{k+1}] = F_k + (f(u_k) + 4 f(u_k + h/2) + f(u_{k+1})) h/6, summed in    */
+/* order.  F has T+1 entries.                                               */
+OR_API void or_erdf_table(const double erdf[6], int kind, int linear_space, double* F)
+{
+    double umin = erdf[0], h = (erdf[1] - erdf[0]) / (double)OR_ERDF_TABLE;
+    double h6 = h / 6.0;
+    F[0] = 0.0;
+    for (int k = 0; k < OR_ERDF_TABLE; ++k) {
+        double u0 = umin + (double)k * h;
+        double u1 = umin + (double)(k + 1) * h;
+        double um = u0 + 0.5 * h;
+        double sum = or_erdf_density(erdf, kind, linear_space, u0)
+                     + 4.0 * or_erdf_density(erdf, kind, linear_space, um);
+        sum = sum + or_erdf_density(erdf, kind, linear_space, u1);
+        F[k + 1] = F[k] + sum * h6;
+    }
+}
+
+/* Inverse of the tabulated CDF: v = U F_T; the interval k with             */
+/* F_k <= v < F_{k+1} by bisection; u linear in v inside it (the density     */
+/* taken constant over one interval); lambda = e^{ln10 u} clamped to the     */
+/* range as in the closed form.                                             */
+OR_API double or_erdf_icdf_tab(const double erdf[6], const double* F, double U)
+{
+    double umin = erdf[0], umax = erdf[1];
+    double h = (umax - umin) / (double)OR_ERDF_TABLE;
+    double v = U * F[OR_ERDF_TABLE];
+    int lo = 0, hi = OR_ERDF_TABLE;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (F[mid] <= v) lo = mid; else hi = mid;
+    }
+    double den = F[lo + 1] - F[lo];
+    double t = den > 0.0 ? (v - F[lo]) / den : 0.0;
+    double u = (umin + (double)lo * h) + t * h;
+    double lam = or_spec_exp(OR_LN10 * u);
+    double lmin = or_spec_exp(OR_LN10 * umin), lmax = or_spec_exp(OR_LN10 * umax);
+    if (lam < lmin) lam = lmin;
+    if (lam > lmax) lam = lmax;
+    return lam;
+}
+
 /* N draws from the ERDF in draw order (Sec. 2.1, second step).  Draw k uses
  * Philox block k/2 of stream 1, words (w0,w1) for even k and (w2,w3) for odd k.
- * prec = 0 rounds each draw to float (round to nearest), prec = 1 keeps it. */
-OR_API void or_erdf_draws(const double erdf[5], int linear_space, uint64_t seed,
+ * kind 0 inverts the sharp form in closed form, kinds 1 and 2 through the
+ * table above.  prec = 0 rounds each draw to float (round to nearest),
+ * prec = 1 keeps it. */
+OR_API void or_erdf_draws(const double erdf[6], int linear_space, int kind, uint64_t seed,
                           uint64_t curve_id, int prec, size_t n, double* out)
 {
     uint32_t w[4];
+    double* F = NULL;
+    if (kind != 0) {
+        F = (double*)malloc(sizeof(double) * (OR_ERDF_TABLE + 1));
+        or_erdf_table(erdf, kind, linear_space, F);
+    }
     for (size_t k = 0; k < n; ++k) {
         if ((k & 1) == 0) philox_block(seed, curve_id, 1u, (uint64_t)(k >> 1), w);
         double U = (k & 1) ? or_u01(w[2], w[3]) : or_u01(w[0], w[1]);
-        double lam = or_erdf_icdf(erdf, linear_space, U);
+        double lam = kind == 0 ? or_erdf_icdf(erdf, linear_space, U) : or_erdf_icdf_tab(erdf, F, U);
         out[k] = prec == 0 ? (double)(float)lam : lam;
     }
+    free(F);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -523,23 +608,24 @@ OR_API uint32_t or_iterate_conv(uint32_t log2n, const double* A, const double* s
 
 /* ------------------------------------------------------------------------ */
 /* Whole generator for one curve.  params[] = {dt, f_br, a_low, a_high,      */
-/* log_lmin, log_lmax, log_lbreak, slope_low, slope_high}.                   */
+/* log_lmin, log_lmax, log_lbreak, slope_low, slope_high, sigma}; kind is    */
+/* the ERDF shape (0 sharp, 1 smooth Eq. 1, 2 log-normal Eq. 2).             */
 /* out_x (n) receives the final series; out_tk (n, nullable) the normalised   */
 /* TK95 series; out_A (n/2+1, nullable) the amplitudes; out_s (n, nullable)  */
 /* the sorted draws.  prec 0 = draws rounded to float, 1 = double.          */
 /* ------------------------------------------------------------------------ */
-OR_API void or_generate(uint32_t log2n, const double params[9], int linear_space,
+OR_API void or_generate(uint32_t log2n, const double params[10], int linear_space, int kind,
                         uint32_t iters, uint64_t seed, uint64_t curve_id, int prec,
                         double* out_x, double* out_tk, double* out_A, double* out_s)
 {
     size_t n = (size_t)1 << log2n, nh = n / 2;
     double psd[3] = {params[1], params[2], params[3]};
-    double erdf[5] = {params[4], params[5], params[6], params[7], params[8]};
+    double erdf[6] = {params[4], params[5], params[6], params[7], params[8], params[9]};
     double* xtk = (double*)malloc(sizeof(double) * n);
     double* A = (double*)malloc(sizeof(double) * (nh + 1));
     double* s = (double*)malloc(sizeof(double) * n);
     or_tk_series(log2n, params[0], psd, seed, curve_id, xtk, A, NULL);
-    or_erdf_draws(erdf, linear_space, seed, curve_id, prec, n, out_x);
+    or_erdf_draws(erdf, linear_space, kind, seed, curve_id, prec, n, out_x);
     memcpy(s, out_x, sizeof(double) * n);
     or_sort(n, s);
     or_iterate(log2n, A, s, out_x, iters, NULL, NULL);
@@ -552,12 +638,12 @@ OR_API void or_generate(uint32_t log2n, const double params[9], int linear_space
 /* ------------------------------------------------------------------------ */
 /* A batch of independent curves on `nthreads` host threads (curves are      */
 /* independent, so this is only a loop split across threads).               */
-/* log2n[c], params[9c..9c+8], linear_space[c], iters[c], seed[c],          */
-/* curve_id[c]; out_x is the concatenation of the curves in order.          */
+/* log2n[c], params[10c..10c+9], linear_space[c], kind[c], iters[c],       */
+/* seed[c], curve_id[c]; out_x is the concatenation of the curves in order. */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     size_t ncurves;
-    const uint32_t* log2n; const double* params; const int* lin; const uint32_t* iters;
+    const uint32_t* log2n; const double* params; const int* lin; const int* kind; const uint32_t* iters;
     const uint64_t* seed; const uint64_t* curve_id; int prec;
     double* out_x; const size_t* offsets;
     size_t next; pthread_mutex_t lock;
@@ -571,21 +657,21 @@ static void* batch_worker(void* arg)
         size_t c = b->next++;
         pthread_mutex_unlock(&b->lock);
         if (c >= b->ncurves) break;
-        or_generate(b->log2n[c], b->params + 9 * c, b->lin[c], b->iters[c], b->seed[c],
+        or_generate(b->log2n[c], b->params + 10 * c, b->lin[c], b->kind[c], b->iters[c], b->seed[c],
                     b->curve_id[c], b->prec, b->out_x + b->offsets[c], NULL, NULL, NULL);
     }
     return NULL;
 }
 
 OR_API int or_generate_batch(size_t ncurves, const uint32_t* log2n, const double* params,
-                             const int* linear_space, const uint32_t* iters,
+                             const int* linear_space, const int* kind, const uint32_t* iters,
                              const uint64_t* seed, const uint64_t* curve_id, int prec,
                              int nthreads, double* out_x)
 {
     size_t* offsets = (size_t*)malloc(sizeof(size_t) * (ncurves + 1));
     offsets[0] = 0;
     for (size_t c = 0; c < ncurves; ++c) offsets[c + 1] = offsets[c] + ((size_t)1 << log2n[c]);
-    batch_ctx b = {ncurves, log2n, params, linear_space, iters, seed, curve_id, prec,
+    batch_ctx b = {ncurves, log2n, params, linear_space, kind, iters, seed, curve_id, prec,
                    out_x, offsets, 0, PTHREAD_MUTEX_INITIALIZER};
     if (nthreads < 1) nthreads = 1;
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);

@@ -493,3 +493,136 @@ def test_iterate_conv_fixed_point():
     assert zeros.size > 0 and np.all(d[zeros[0]:] == 0.0)
     _, _, run_t = oracle.iterate_conv(A, s, x0, 60, 1e-300)
     assert run_t == zeros[0] + 1
+
+
+# ------------------------------------- tabulated ERDF shapes (Eq. 1 smooth, Eq. 2)
+def _golden():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.json")) as f:
+        return json.load(f)
+
+
+def _lognormal_erdf():
+    w = _golden()["erdf_log_normal_eq2"]
+    return np.array([-4.0, 0.0, w["log_lambda_star"], 0.0, 0.0, w["sigma"]])
+
+
+def _smooth_erdf():
+    w = _golden()["erdf_broken_power_law_eq1"]
+    return np.array([-3.75, 0.5, w["log_lambda_star"], -w["delta1"], -w["delta2"], 0.0])
+
+
+def _grid(e):
+    return e[0] + np.arange(oracle.ERDF_TABLE + 1) * ((e[1] - e[0]) / oracle.ERDF_TABLE)
+
+
+@pytest.mark.parametrize("lin", [0, 1])
+def test_lognormal_table_is_the_truncated_normal_cdf(lin):
+    """Eq. 2 in u = log10 lambda is a normal density (mean log lambda*, sd
+    sigma-tilde); its CDF is the textbook Phi.  With linear_space the extra
+    factor 10^u shifts the mean by sigma^2 ln 10 (completing the square)."""
+    from scipy.special import ndtr
+    e = _lognormal_erdf()
+    F = oracle.erdf_table(e, 2, lin)
+    mu = e[2] + (e[5] ** 2 * math.log(10.0) if lin else 0.0)
+    G = ndtr((_grid(e) - mu) / e[5])
+    G = G - G[0]
+    assert F[0] == 0.0 and np.all(np.diff(F) > 0)
+    np.testing.assert_allclose(F / F[-1], G / G[-1], rtol=0, atol=1e-12)
+    # the unnormalised scale is the integral of exp(-(u-mu)^2/(2 s^2)), times
+    # exp((s ln 10)^2 / 2) with lin (the constant left over by completing the square)
+    scale = e[5] * math.sqrt(2 * math.pi) * (math.exp((e[5] * math.log(10.0)) ** 2 / 2) if lin else 1.0)
+    assert F[-1] == pytest.approx(scale * G[-1], rel=1e-10)
+
+
+def test_lognormal_inverse_matches_ndtri():
+    """Bisection plus linear interpolation inverts the table to within the
+    interpolation error of one interval (h = 1/1024 dex): |du| < 2e-6 dex."""
+    from scipy.special import ndtr, ndtri
+    e = _lognormal_erdf()
+    F = oracle.erdf_table(e, 2)
+    U = np.concatenate([[2.0 ** -53, 1e-9, 1 - 1e-9], np.linspace(1e-6, 1 - 1e-6, 4001)])
+    lam = oracle.erdf_icdf_tab(e, F, U)
+    a, b = ndtr((e[0] - e[2]) / e[5]), ndtr((e[1] - e[2]) / e[5])
+    u_exact = e[2] + e[5] * ndtri(a + U * (b - a))
+    assert np.max(np.abs(np.log10(lam) - u_exact)) < 2e-6
+    assert np.all(np.diff(lam[3:]) >= 0)
+
+
+@pytest.mark.parametrize("lin", [0, 1])
+def test_table_inverse_of_the_sharp_form_matches_its_closed_form(lin):
+    """The tabulated path applied to the sharp broken power law (a case with a
+    closed-form inverse) agrees with the closed form to 2e-6 dex."""
+    e = np.concatenate([ERDF_BASE, [0.0]])
+    F = oracle.erdf_table(e, 0, lin)
+    U = np.linspace(1e-6, 1 - 1e-6, 4001)
+    t = np.log10(oracle.erdf_icdf_tab(e, F, U))
+    c = np.log10(oracle.erdf_icdf(ERDF_BASE, U, linear_space=lin))
+    assert np.max(np.abs(t - c)) < 2e-6
+
+
+@pytest.mark.parametrize("lin", [0, 1])
+def test_smooth_eq1_table_matches_quadrature(lin):
+    """Eq. 1 with the paper's W17 values (golden fixture), written from the
+    paper as a function of lambda, integrated by scipy's adaptive quadrature:
+    the table's node values agree to 1e-9 (relative to the total)."""
+    from scipy.integrate import quad
+    w = _golden()["erdf_broken_power_law_eq1"]
+    e = _smooth_erdf()
+    F = oracle.erdf_table(e, 1, lin)
+    lam_star = 10.0 ** w["log_lambda_star"]
+
+    def xi(u):  # dN/dlog10(lambda); times lambda/lambda* for the dN/dlambda reading
+        r = 10.0 ** u / lam_star
+        v = 1.0 / (r ** w["delta1"] + r ** w["delta2"])
+        return v * r if lin else v
+
+    nodes = _grid(e)[::256]
+    G = np.zeros(nodes.size)
+    for i in range(1, nodes.size):
+        G[i] = G[i - 1] + quad(xi, nodes[i - 1], nodes[i], epsabs=0, epsrel=1e-13, limit=200)[0]
+    np.testing.assert_allclose(F[::256], G, rtol=0, atol=1e-9 * G[-1])
+
+
+def test_smooth_eq1_density_limits():
+    """Eq. 1 is half the sharp form at the break and tends to the sharp form's
+    branches away from it (within 1e-4 at 2 dex for the W17 slopes)."""
+    e = _smooth_erdf()
+    assert oracle.erdf_density(e, e[2], 1)[0] == 0.5
+    for d in (-2.0, -2.5, 2.0, 2.4):
+        u = e[2] + d
+        r = oracle.erdf_density(e, u, 1)[0] / oracle.erdf_density(e, u, 0)[0]
+        assert 1 - 1e-4 < r <= 1.0
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_tabulated_draws_follow_the_exact_cdf(kind):
+    """KS distance of 2^17 draws against the exact CDF (Phi for Eq. 2,
+    quadrature for Eq. 1); draws stay in range; FP32 draws are the RN
+    roundings of the FP64 ones."""
+    from scipy.special import ndtr
+    e = _lognormal_erdf() if kind == 2 else _smooth_erdf()
+    n = 1 << 17
+    x = oracle.erdf_draws(e, n, seed=7, curve_id=2, prec=1, kind=kind)
+    assert x.min() >= 10 ** e[0] * (1 - 1e-15) and x.max() <= 10 ** e[1] * (1 + 1e-15)
+    u = np.log10(np.sort(x))
+    if kind == 2:
+        a, b = ndtr((e[0] - e[2]) / e[5]), ndtr((e[1] - e[2]) / e[5])
+        Fx = (ndtr((u - e[2]) / e[5]) - a) / (b - a)
+    else:
+        grid, cdf = _cdf_table_smooth(e)
+        Fx = np.interp(u, grid, cdf)
+    emp = np.arange(1, n + 1) / n
+    D = max(np.max(emp - Fx), np.max(Fx - (emp - 1.0 / n)))
+    assert D < 1.95 / math.sqrt(n)
+    x32 = oracle.erdf_draws(e, 4096, seed=7, curve_id=2, prec=0, kind=kind)
+    assert np.array_equal(x32, x[:4096].astype(np.float32).astype(np.float64))
+
+
+def _cdf_table_smooth(e):
+    """Exact-enough CDF of Eq. 1 on a fine grid by composite trapezoid on 2^18 points."""
+    w = _golden()["erdf_broken_power_law_eq1"]
+    u = np.linspace(e[0], e[1], (1 << 18) + 1)
+    r = 10.0 ** (u - w["log_lambda_star"])
+    f = 1.0 / (r ** w["delta1"] + r ** w["delta2"])
+    c = np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(u))])
+    return u, c / c[-1]
