@@ -69,11 +69,27 @@ typedef struct {
     double alpha_high;
 } lc_psd;
 
-/* ERDF: a broken power law in u = log10(lambda) on [log_lmin, log_lmax] with a
- * sharp break at log_lbreak (the sharp-break form of Eq. 1):
- * dN/dlog10(lambda) ~ lambda^slope_low below and lambda^slope_high above the
- * break.  linear_space != 0 states the slopes for dN/dlambda instead (the
- * linear sampling of Sec. 2.1.1), i.e. both are raised by one in log space. */
+/* Shape of the ERDF (Sec. 2.1.1). */
+typedef enum {
+    LC_ERDF_SHARP = 0,     /* broken power law with a sharp break (closed-form inverse CDF) */
+    LC_ERDF_SMOOTH = 1,    /* the smooth broken power law of Eq. 1 (tabulated CDF)          */
+    LC_ERDF_LOGNORMAL = 2  /* the log-normal of Eq. 2 (tabulated CDF)                        */
+} lc_erdf_kind;
+
+/* ERDF on u = log10(lambda) in [log_lmin, log_lmax], with d = u - log_lbreak:
+ *   LC_ERDF_SHARP:     dN/du ~ 10^(slope_low d) for d < 0, 10^(slope_high d) above;
+ *   LC_ERDF_SMOOTH:    dN/du ~ [10^(-slope_low d) + 10^(-slope_high d)]^-1, i.e.
+ *                      Eq. 1 with log lambda* = log_lbreak, delta_1 = -slope_low,
+ *                      delta_2 = -slope_high (W17: -0.47, -2.53);
+ *   LC_ERDF_LOGNORMAL: dN/du ~ exp(-d^2 / (2 sigma^2)), i.e. Eq. 2 with
+ *                      log lambda* = log_lbreak and sigma-tilde = sigma (dex).
+ * linear_space != 0 reads the shape as dN/dlambda instead (the linear sampling
+ * of Sec. 2.1.1): the density in u gains a factor 10^d (for the power laws
+ * both slopes rise by one).  The sharp form is inverted in closed form; the
+ * other two through an FP64 table of their CDF (4096 intervals of Simpson's
+ * rule, bisection and linear interpolation, inverse error < 1e-6 dex), with
+ * the same bits on the GPU and in any IEEE-754 reimplementation that follows
+ * the same operation order.  Zero-initialised fields give the sharp form. */
 typedef struct {
     double log_lmin;
     double log_lmax;
@@ -81,6 +97,8 @@ typedef struct {
     double slope_low;
     double slope_high;
     int32_t linear_space;
+    int32_t kind;          /* lc_erdf_kind */
+    double sigma;          /* LC_ERDF_LOGNORMAL width in dex; unused otherwise */
 } lc_erdf;
 
 /* One light curve (the inputs of Sec. 3.2.4: t_bin = dt, N_steps = 2^log2n).
@@ -113,8 +131,11 @@ LC_API const char* lc_last_error(void);
  * the ragged layout, twiddle tables and every device workspace the batch
  * needs (allocated here, owned by the plan).  jobs: host array, read only
  * during the call.  Validation: njobs >= 1, 4 <= log2n <= 27, dt > 0,
- * f_br > 0, finite slopes, log_lmin < log_lbreak < log_lmax; otherwise
- * LC_ERR_INVALID.  LC_ERR_NOMEM if the workspace does not fit.  Blocking. */
+ * f_br > 0, finite slopes, -300 <= log_lmin < log_lmax <= 300; for the power
+ * laws log_lmin < log_lbreak < log_lmax and |slope| <= 50; for the log-normal
+ * sigma >= (log_lmax - log_lmin)/1024 and the centre log_lbreak within 30
+ * sigma of the range; otherwise LC_ERR_INVALID.  LC_ERR_NOMEM if the
+ * workspace does not fit.  Blocking. */
 LC_API lc_status lc_plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device,
                          lc_plan* out);
 

@@ -27,9 +27,12 @@ class LcPsd(ctypes.Structure):
     _fields_ = [("f_br", c_d), ("alpha_low", c_d), ("alpha_high", c_d)]
 
 
+LC_ERDF_SHARP, LC_ERDF_SMOOTH, LC_ERDF_LOGNORMAL = 0, 1, 2
+
+
 class LcErdf(ctypes.Structure):
     _fields_ = [("log_lmin", c_d), ("log_lmax", c_d), ("log_lbreak", c_d), ("slope_low", c_d),
-                ("slope_high", c_d), ("linear_space", c_i32)]
+                ("slope_high", c_d), ("linear_space", c_i32), ("kind", c_i32), ("sigma", c_d)]
 
 
 class LcJob(ctypes.Structure):
@@ -136,7 +139,8 @@ def make_job(j) -> LcJob:
     return LcJob(int(j["log2n"]), int(j["iters"]), float(j["dt"]),
                  LcPsd(float(j["f_br"]), float(j["alpha_low"]), float(j["alpha_high"])),
                  LcErdf(float(j["log_lmin"]), float(j["log_lmax"]), float(j["log_lbreak"]),
-                        float(j["slope_low"]), float(j["slope_high"]), int(j.get("linear_space", 0))),
+                        float(j["slope_low"]), float(j["slope_high"]), int(j.get("linear_space", 0)),
+                        int(j.get("erdf_kind", 0)), float(j.get("sigma", 0.0))),
                  int(j["seed"]), int(j["curve_id"]))
 
 

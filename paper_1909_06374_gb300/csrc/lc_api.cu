@@ -75,14 +75,39 @@ lc_status validate_job(const lc_job& j)
     if (!(j.psd.f_br > 0) || !finite(j.psd.f_br)) { set_error("f_br must be > 0"); return LC_ERR_INVALID; }
     if (!finite(j.psd.alpha_low) || !finite(j.psd.alpha_high)) { set_error("PSD slopes must be finite"); return LC_ERR_INVALID; }
     const lc_erdf& e = j.erdf;
+    if (e.kind < LC_ERDF_SHARP || e.kind > LC_ERDF_LOGNORMAL) { set_error("unknown ERDF kind"); return LC_ERR_INVALID; }
     if (!finite(e.log_lmin) || !finite(e.log_lmax) || !finite(e.log_lbreak) || !finite(e.slope_low) ||
         !finite(e.slope_high)) { set_error("ERDF parameters must be finite"); return LC_ERR_INVALID; }
+    if (!(e.log_lmin < e.log_lmax)) { set_error("ERDF needs log_lmin < log_lmax"); return LC_ERR_INVALID; }
+    if (e.log_lmin < -300 || e.log_lmax > 300) { set_error("ERDF range out of [1e-300, 1e300]"); return LC_ERR_INVALID; }
+    if (e.kind == LC_ERDF_LOGNORMAL) {
+        // the table resolves the bell (>= 4 intervals per sigma) and holds mass
+        if (!finite(e.sigma) || !(e.sigma >= (e.log_lmax - e.log_lmin) / 1024.0)) {
+            set_error("log-normal ERDF needs sigma >= (log_lmax - log_lmin)/1024"); return LC_ERR_INVALID;
+        }
+        if (e.log_lbreak < e.log_lmin - 30.0 * e.sigma || e.log_lbreak > e.log_lmax + 30.0 * e.sigma) {
+            set_error("log-normal ERDF centre more than 30 sigma outside the range"); return LC_ERR_INVALID;
+        }
+        return LC_OK;
+    }
     if (!(e.log_lmin < e.log_lbreak && e.log_lbreak < e.log_lmax)) {
         set_error("ERDF needs log_lmin < log_lbreak < log_lmax"); return LC_ERR_INVALID;
     }
-    if (e.log_lmin < -300 || e.log_lmax > 300) { set_error("ERDF range out of [1e-300, 1e300]"); return LC_ERR_INVALID; }
     if (std::fabs(e.slope_low) > 50 || std::fabs(e.slope_high) > 50) { set_error("ERDF slope magnitude > 50"); return LC_ERR_INVALID; }
     return LC_OK;
+}
+
+CurveDev curve_from_job(const lc_job& j)
+{
+    CurveDev cv{};
+    cv.log2n = j.log2n; cv.iters = j.iters;
+    cv.dt = j.dt; cv.f_br = j.psd.f_br; cv.a_lo = j.psd.alpha_low; cv.a_hi = j.psd.alpha_high;
+    cv.umin = j.erdf.log_lmin; cv.umax = j.erdf.log_lmax; cv.ub = j.erdf.log_lbreak;
+    cv.sl_lo = j.erdf.slope_low; cv.sl_hi = j.erdf.slope_high; cv.lin = j.erdf.linear_space ? 1 : 0;
+    cv.kind = j.erdf.kind;
+    cv.sigma = j.erdf.kind == LC_ERDF_LOGNORMAL ? j.erdf.sigma : 0.0;
+    cv.seed = j.seed; cv.curve_id = j.curve_id;
+    return cv;
 }
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -138,11 +163,8 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     for (size_t c = 0; c < njobs; ++c) {
         const lc_job& j = jobs[c];
         CurveDev& cv = p->h_curves[c];
-        cv.off = off; cv.offh = offh; cv.log2n = j.log2n; cv.iters = j.iters;
-        cv.dt = j.dt; cv.f_br = j.psd.f_br; cv.a_lo = j.psd.alpha_low; cv.a_hi = j.psd.alpha_high;
-        cv.umin = j.erdf.log_lmin; cv.umax = j.erdf.log_lmax; cv.ub = j.erdf.log_lbreak;
-        cv.sl_lo = j.erdf.slope_low; cv.sl_hi = j.erdf.slope_high; cv.lin = j.erdf.linear_space ? 1 : 0;
-        cv.seed = j.seed; cv.curve_id = j.curve_id;
+        cv = curve_from_job(j);
+        cv.off = off; cv.offh = offh;
         if (cls_of_len[j.log2n] < 0) {
             cls_of_len[j.log2n] = (int)p->classes.size();
             p->classes.emplace_back();
@@ -150,6 +172,11 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         }
         cv.cls = cls_of_len[j.log2n];
         p->classes[cv.cls].h_curves.push_back((int)c);
+        if (cv.kind != LC_ERDF_SHARP) {
+            cv.tab = (uint64_t)p->ntab * (kErdfTable + 1);
+            ++p->ntab;
+            p->classes[cv.cls].h_tab_curves.push_back((int)c);
+        }
         off += 1ull << j.log2n;
         offh += (1ull << (j.log2n - 1)) + 1;
         p->max_iters = std::max(p->max_iters, j.iters);
@@ -191,6 +218,8 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     const size_t o_cbase = take(sizeof(uint32_t) * cbase);
     const size_t o_tw = take(twb);
     const size_t o_cls = take(sizeof(int) * njobs);
+    const size_t o_tabc = take(sizeof(int) * 2 * p->ntab);  // all, then per class
+    const size_t o_tab = take(sizeof(double) * (kErdfTable + 1) * p->ntab);
     const size_t o_rx = prec == LC_FP32 ? take(rxb) : 0;
     p->arena_bytes = sz;
     if (cudaMalloc(&p->arena, sz) != cudaSuccess) {
@@ -230,6 +259,19 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         }
     }
     p->tw_bytes = twb;
+    std::vector<int> tab_all, tab_cls;
+    if (p->ntab) {
+        p->d_tab = (double*)(base + o_tab);
+        p->d_tab_curves = (int*)(base + o_tabc);
+        for (size_t c = 0; c < njobs; ++c)
+            if (p->h_curves[c].kind != LC_ERDF_SHARP) tab_all.push_back((int)c);
+        for (auto& k : p->classes) {
+            k.ntab = (int)k.h_tab_curves.size();
+            k.d_tab_curves = p->d_tab_curves + p->ntab + tab_cls.size();
+            tab_cls.insert(tab_cls.end(), k.h_tab_curves.begin(), k.h_tab_curves.end());
+        }
+        tab_all.insert(tab_all.end(), tab_cls.begin(), tab_cls.end());
+    }
 
     auto fail = [&](const char* what, cudaError_t e) {
         set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -251,6 +293,9 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         if ((e = cudaMemcpyAsync(k.d_curves, k.h_curves.data(), sizeof(int) * k.h_curves.size(),
                                  cudaMemcpyHostToDevice, p->stream)) != cudaSuccess) return fail("upload classes", e);
     }
+    if (p->ntab && (e = cudaMemcpyAsync(p->d_tab_curves, tab_all.data(), sizeof(int) * tab_all.size(),
+                                        cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
+        return fail("upload table curves", e);
     lc_status st = prec == LC_FP32 ? build_tables<float>(*p) : build_tables<double>(*p);
     if (st != LC_OK) { cudaFree(p->arena); delete p; return st; }
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail("plan sync", e);
@@ -279,7 +324,11 @@ static lc_status run_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* lau
     }
     launch_erdf_constants(p, st);
     ++*launches;
-    for (auto& k : p.classes) { launch_erdf_draws<T>(p, k, st); ++*launches; }
+    if (p.ntab) {
+        launch_erdf_tables(p, st);
+        ++*launches;
+    }
+    for (auto& k : p.classes) { launch_erdf_draws<T>(p, k, st); *launches += (k.ntab < k.ncurves) + (k.ntab > 0); }
     for (auto& k : p.classes) launch_sort<T>(p, k, p.d_x, kSortKeysToValues, false, st, launches);
     cudaEventRecord(p.t_setup1, st);
     LC_CK(cudaGetLastError());

@@ -21,6 +21,10 @@ struct CurveDev {
     int32_t lin;
     int32_t cls;
     uint64_t seed, curve_id;
+    int32_t kind;                         // lc_erdf_kind
+    int32_t pad;
+    double sigma;                         // log-normal width (dex)
+    uint64_t tab;                         // tabulated shapes: offset of the CDF table (doubles)
 };
 
 // Per-curve constants of the ERDF inverse CDF (computed once per curve on the
@@ -264,6 +268,74 @@ __device__ __forceinline__ double erdf_draw(const ErdfConst& k, double U)
     double lam = spec_exp(__dmul_rn(LC_LN10, u));
     if (lam < k.lo) lam = k.lo;
     if (lam > k.hi) lam = k.hi;
+    return lam;
+}
+
+// ---------------------------------------- tabulated ERDF shapes (Eq. 1, Eq. 2)
+// The smooth broken power law of Eq. 1 and the log-normal of Eq. 2 have no
+// closed-form inverse CDF.  Their unnormalised CDF is tabulated on
+// kErdfTable uniform intervals of u = log10(lambda) (Simpson's rule per
+// interval, accumulated in order by one thread), inverted by bisection and
+// linear interpolation inside the interval.  Every step is a correctly
+// rounded operation with the order fixed, so the table and the draws have the
+// same bits in any IEEE reimplementation of the same sequence.
+constexpr int kErdfTable = 4096;
+
+// Density in u, up to a constant: with d = u - ub,
+//   kind 1: [e^{-c1 d} + e^{-c2 d}]^-1, c = slope ln10 (+ ln10 with lin);
+//   kind 2: e^{-(d/sigma)^2/2} (times e^{ln10 d} with lin).
+__device__ inline double erdf_density(const CurveDev& cv, double u)
+{
+    const double d = __dsub_rn(u, cv.ub);
+    if (cv.kind == 1) {
+        double a1 = cv.sl_lo, a2 = cv.sl_hi;
+        if (cv.lin) { a1 = __dadd_rn(a1, 1.0); a2 = __dadd_rn(a2, 1.0); }
+        const double c1 = __dmul_rn(a1, LC_LN10), c2 = __dmul_rn(a2, LC_LN10);
+        return __ddiv_rn(1.0, __dadd_rn(spec_exp(__dmul_rn(-c1, d)), spec_exp(__dmul_rn(-c2, d))));
+    }
+    const double t = __ddiv_rn(d, cv.sigma);
+    double e = __dmul_rn(__dmul_rn(-0.5, t), t);
+    if (cv.lin) e = __dadd_rn(e, __dmul_rn(LC_LN10, d));
+    return spec_exp(e);
+}
+
+__device__ __forceinline__ double erdf_table_step(const CurveDev& cv)
+{
+    return __ddiv_rn(__dsub_rn(cv.umax, cv.umin), (double)kErdfTable);
+}
+
+// Simpson's rule on interval k: (f(u_k) + 4 f(u_k + h/2) + f(u_{k+1})) h/6,
+// u_k = umin + k h.
+__device__ inline double erdf_table_interval(const CurveDev& cv, int k)
+{
+    const double h = erdf_table_step(cv);
+    const double h6 = __ddiv_rn(h, 6.0);
+    const double u0 = __dadd_rn(cv.umin, __dmul_rn((double)k, h));
+    const double u1 = __dadd_rn(cv.umin, __dmul_rn((double)(k + 1), h));
+    const double um = __dadd_rn(u0, __dmul_rn(0.5, h));
+    double sum = __dadd_rn(erdf_density(cv, u0), __dmul_rn(4.0, erdf_density(cv, um)));
+    sum = __dadd_rn(sum, erdf_density(cv, u1));
+    return __dmul_rn(sum, h6);
+}
+
+// Inverse of the tabulated CDF F[0..kErdfTable] (F in any memory space):
+// v = U F_T, interval k with F_k <= v < F_{k+1}, u linear in v inside it,
+// lambda = e^{ln10 u} clamped to [lo, hi].
+__device__ __forceinline__ double erdf_draw_tab(const double* F, double umin, double h, double lo, double hi,
+                                                double U)
+{
+    const double v = __dmul_rn(U, F[kErdfTable]);
+    int a = 0, b = kErdfTable;
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (F[mid] <= v) a = mid; else b = mid;
+    }
+    const double den = __dsub_rn(F[a + 1], F[a]);
+    const double t = den > 0.0 ? __ddiv_rn(__dsub_rn(v, F[a]), den) : 0.0;
+    const double u = __dadd_rn(__dadd_rn(umin, __dmul_rn((double)a, h)), __dmul_rn(t, h));
+    double lam = spec_exp(__dmul_rn(LC_LN10, u));
+    if (lam < lo) lam = lo;
+    if (lam > hi) lam = hi;
     return lam;
 }
 

@@ -30,6 +30,9 @@ struct ClassInfo {
     size_t partial_off = 0;            // into d_partial (double)
     bool resident = false;             // iterated by the fused on-chip kernel
     float* d_rx = nullptr;             // L2 exchange area of the cluster kernel (3 N floats per curve)
+    int ntab = 0;                      // curves with a tabulated ERDF (Eq. 1 smooth, Eq. 2)
+    int* d_tab_curves = nullptr;       // their curve indices (device)
+    std::vector<int> h_tab_curves;
 };
 
 struct Plan {
@@ -65,6 +68,9 @@ struct Plan {
     uint32_t* d_cbase = nullptr;
     size_t tw_bytes = 0;
     void* d_tk_stage = nullptr;  // lazily allocated for lc_generate_host
+    size_t ntab = 0;             // curves with a tabulated ERDF
+    int* d_tab_curves = nullptr; // their indices (device)
+    double* d_tab = nullptr;     // their CDF tables, kErdfTable + 1 doubles each
 
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -91,6 +97,8 @@ int spec_blocks_per_curve(uint32_t log2n);
 void launch_tk_spectrum(const Plan& p, const ClassInfo& k, cudaStream_t st);
 template <typename T> void launch_amplitudes(const Plan& p, const ClassInfo& k, cudaStream_t st);
 void launch_erdf_constants(const Plan& p, cudaStream_t st);
+// CDF tables of every curve with a tabulated ERDF shape (before the draws)
+void launch_erdf_tables(const Plan& p, cudaStream_t st);
 template <typename T> void launch_erdf_draws(const Plan& p, const ClassInfo& k, cudaStream_t st);
 
 // FFT stage (lc_fft.cu)
@@ -146,6 +154,8 @@ void launch_eff_iters(const Plan& p, uint32_t override_iters, cudaStream_t st);
 void set_error(const std::string& msg);
 const char* last_error_text();
 lc_status validate_job(const lc_job& j);
+// Curve descriptor of a job (offsets, class and table offset left to the caller).
+CurveDev curve_from_job(const lc_job& j);
 
 // plan life cycle shared by the batch ABI and the server
 lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device, Plan** out);

@@ -71,12 +71,9 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     p.ncurves = 1;
     p.path_mode = path_mode_from_env();
     const size_t n = (size_t)1 << job->log2n, nh = n / 2 + 1, ts = 4;
-    CurveDev cv{};
-    cv.off = 0; cv.offh = 0; cv.log2n = job->log2n; cv.iters = job->iters;
-    cv.dt = job->dt; cv.f_br = job->psd.f_br; cv.a_lo = job->psd.alpha_low; cv.a_hi = job->psd.alpha_high;
-    cv.umin = job->erdf.log_lmin; cv.umax = job->erdf.log_lmax; cv.ub = job->erdf.log_lbreak;
-    cv.sl_lo = job->erdf.slope_low; cv.sl_hi = job->erdf.slope_high; cv.lin = job->erdf.linear_space ? 1 : 0;
-    cv.cls = 0; cv.seed = job->seed; cv.curve_id = job->curve_id;
+    CurveDev cv = curve_from_job(*job);
+    cv.off = 0; cv.offh = 0; cv.cls = 0; cv.tab = 0;
+    const bool tabulated = cv.kind != LC_ERDF_SHARP;
     p.h_curves.assign(1, cv);
     p.total = n; p.total_h = nh; p.max_iters = job->iters;
     p.classes.emplace_back();
@@ -115,6 +112,14 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     k.d_tw = take((n / 2) * 2 * ts);
     k.d_curves = (int*)take(sizeof(int));
     if (resident_exchange_floats(k.log2n)) k.d_rx = (float*)take(resident_exchange_floats(k.log2n) * 4);
+    if (tabulated) {
+        // the CDF table of a smooth (Eq. 1) or log-normal (Eq. 2) ERDF
+        p.ntab = 1;
+        k.ntab = 1;
+        p.d_tab = (double*)take(sizeof(double) * (kErdfTable + 1));
+        p.d_tab_curves = k.d_curves;  // the one curve, index 0
+        k.d_tab_curves = k.d_curves;
+    }
     if (at > kNoallocBytes) { set_error("lc_generate_noalloc: layout exceeds the static scratch"); return LC_ERR_INVALID; }
 
     // descriptors (pageable host source: the copy is staged before the call returns)
@@ -130,6 +135,7 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     launch_tk_spectrum(p, k, s);
     launch_amplitudes<float>(p, k, s);
     launch_erdf_constants(p, s);
+    launch_erdf_tables(p, s);
     launch_erdf_draws<float>(p, k, s);
     launch_sort<float>(p, k, p.d_x, kSortKeysToValues, false, s, nullptr);
     // iterations (Sec. 3.2.2), launched directly (no graph)

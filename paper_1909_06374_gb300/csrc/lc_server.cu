@@ -88,6 +88,7 @@ static size_t job_footprint(const lc_job& j, lc_precision prec)
     size_t b = 4 * n * ts;                                  // x, f, s, A (upper bound)
     b += std::max(2 * n * ts + 2 * n * 4, 16 * nh);         // sort buffers / FP64 spectrum
     b += tiles * 256 * 4 * 2 + n / 2 * 2 * ts + 64 * 1024;  // histograms, twiddles, descriptors
+    if (j.erdf.kind != LC_ERDF_SHARP) b += sizeof(double) * (kErdfTable + 1);  // ERDF CDF table
     return b;
 }
 

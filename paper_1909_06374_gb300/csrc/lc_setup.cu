@@ -113,10 +113,57 @@ __global__ void k_erdf_draws(const CurveDev* __restrict__ curves, const int* __r
         const uint64_t q = t & (half - 1);
         const int c = cls_curves[ci];
         const CurveDev& cv = curves[c];
+        if (cv.kind != 0) continue;  // tabulated shapes: k_erdf_draws_tab
         const ErdfConst k = ek[c];
         const uint4 w = philox(q, cv.curve_id, 1u, cv.seed);
         const double l0 = erdf_draw(k, unit_open(w.x, w.y));
         const double l1 = erdf_draw(k, unit_open(w.z, w.w));
+        x[cv.off + 2 * q] = (T)l0;
+        x[cv.off + 2 * q + 1] = (T)l1;
+    }
+}
+
+// CDF tables of the tabulated ERDF shapes, one block per curve: the
+// intervals in parallel, then their sum in order by one thread.
+__global__ void __launch_bounds__(256) k_erdf_table(const CurveDev* __restrict__ curves,
+                                                    const int* __restrict__ tab_curves, double* __restrict__ tab)
+{
+    __shared__ double I[kErdfTable];
+    const CurveDev& cv = curves[tab_curves[blockIdx.x]];
+    for (int k = threadIdx.x; k < kErdfTable; k += blockDim.x) I[k] = erdf_table_interval(cv, k);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* F = tab + cv.tab;
+        double acc = 0.0;
+        F[0] = 0.0;
+        for (int k = 0; k < kErdfTable; ++k) {
+            acc = __dadd_rn(acc, I[k]);
+            F[k + 1] = acc;
+        }
+    }
+}
+
+// Draws of the tabulated shapes: a block stages its curve's table in shared
+// memory and inverts `pairs` Philox blocks (same stream and word use as
+// k_erdf_draws).
+template <typename T>
+__global__ void __launch_bounds__(256) k_erdf_draws_tab(const CurveDev* __restrict__ curves,
+                                                        const int* __restrict__ tab_cls_curves, int chunks,
+                                                        uint64_t pairs, const ErdfConst* __restrict__ ek,
+                                                        const double* __restrict__ tab, T* __restrict__ x)
+{
+    __shared__ double F[kErdfTable + 1];
+    const int c = tab_cls_curves[blockIdx.x / chunks];
+    const uint64_t q0 = (uint64_t)(blockIdx.x % chunks) * pairs;
+    const CurveDev& cv = curves[c];
+    for (int i = threadIdx.x; i <= kErdfTable; i += blockDim.x) F[i] = tab[cv.tab + i];
+    __syncthreads();
+    const ErdfConst k = ek[c];
+    const double h = erdf_table_step(cv);
+    for (uint64_t q = q0 + threadIdx.x; q < q0 + pairs; q += blockDim.x) {
+        const uint4 w = philox(q, cv.curve_id, 1u, cv.seed);
+        const double l0 = erdf_draw_tab(F, cv.umin, h, k.lo, k.hi, unit_open(w.x, w.y));
+        const double l1 = erdf_draw_tab(F, cv.umin, h, k.lo, k.hi, unit_open(w.z, w.w));
         x[cv.off + 2 * q] = (T)l0;
         x[cv.off + 2 * q + 1] = (T)l1;
     }
@@ -160,12 +207,27 @@ void launch_erdf_constants(const Plan& p, cudaStream_t st)
     k_erdf_constants<<<(int)((p.ncurves + 127) / 128), 128, 0, st>>>(p.d_curves, (int)p.ncurves, p.d_erdf);
 }
 
+void launch_erdf_tables(const Plan& p, cudaStream_t st)
+{
+    if (p.ntab) k_erdf_table<<<(int)p.ntab, 256, 0, st>>>(p.d_curves, p.d_tab_curves, p.d_tab);
+}
+
 template <typename T>
 void launch_erdf_draws(const Plan& p, const ClassInfo& k, cudaStream_t st)
 {
-    const uint64_t work = (uint64_t)k.ncurves << (k.log2n - 1);
-    k_erdf_draws<T><<<grid_for(work, 256), 256, 0, st>>>(p.d_curves, k.d_curves, k.ncurves, k.log2n,
-                                                         p.d_erdf, (T*)p.d_x);
+    if (k.ntab < k.ncurves) {
+        const uint64_t work = (uint64_t)k.ncurves << (k.log2n - 1);
+        k_erdf_draws<T><<<grid_for(work, 256), 256, 0, st>>>(p.d_curves, k.d_curves, k.ncurves, k.log2n,
+                                                             p.d_erdf, (T*)p.d_x);
+    }
+    if (k.ntab) {
+        // up to 8192 Philox blocks (16384 draws) per block of threads
+        const uint64_t half = 1ull << (k.log2n - 1);
+        const uint64_t pairs = half < 8192 ? half : 8192;
+        const int chunks = (int)(half / pairs);
+        k_erdf_draws_tab<T><<<k.ntab * chunks, 256, 0, st>>>(p.d_curves, k.d_tab_curves, chunks, pairs, p.d_erdf,
+                                                             p.d_tab, (T*)p.d_x);
+    }
 }
 
 template void launch_amplitudes<float>(const Plan&, const ClassInfo&, cudaStream_t);

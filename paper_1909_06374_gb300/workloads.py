@@ -18,6 +18,14 @@ Workloads (all lengths are powers of two, Sec. 3.2.3; dt in days):
 Base PSD (Eq. 3): f_br = 1/300 d^-1, alpha_low = 1, alpha_high = 2.
 Base ERDF (sharp broken power law in log10 lambda): [-4, 0], break -1.5,
 slopes +0.4 below and -2.5 above (dN/dlog10 lambda ~ lambda^slope).
+
+ERDF shapes printed in the paper (Sec. 2.1.1, Sec. 4.1 Table 2), as job
+parameter overrides (ERDF_SHAPES):
+  smooth_eq1  Eq. 1 with W17's log lambda* = -1.84, delta 0.47 / 2.53, on the
+              range W17 probes, log lambda in [-4, 1]
+  table2      Eq. 1 as in the reference setup of Table 2: lambda* = 0.11,
+              delta 0.47 / 2.53, log lambda in [-3.75, 0.5]
+  lognormal   Eq. 2 with log lambda* = -3.25, sigma = 0.64, on [-4, 1]
 """
 from __future__ import annotations
 
@@ -25,7 +33,16 @@ import numpy as np
 
 BASE = dict(dt=1.0, f_br=1.0 / 300.0, alpha_low=1.0, alpha_high=2.0,
             log_lmin=-4.0, log_lmax=0.0, log_lbreak=-1.5, slope_low=0.4, slope_high=-2.5,
-            linear_space=0)
+            linear_space=0, erdf_kind=0, sigma=0.0)
+
+ERDF_SHAPES = {
+    "smooth_eq1": dict(erdf_kind=1, log_lmin=-4.0, log_lmax=1.0, log_lbreak=-1.84,
+                       slope_low=-0.47, slope_high=-2.53),
+    "table2": dict(erdf_kind=1, log_lmin=-3.75, log_lmax=0.5, log_lbreak=float(np.log10(0.11)),
+                   slope_low=-0.47, slope_high=-2.53),
+    "lognormal": dict(erdf_kind=2, log_lmin=-4.0, log_lmax=1.0, log_lbreak=-3.25, sigma=0.64,
+                      slope_low=0.0, slope_high=0.0),
+}
 
 
 def job(log2n, iters, seed, curve_id, **over):

@@ -48,9 +48,10 @@ def test_struct_layout_matches_c():
     #include <stddef.h>
     #include "agnlc.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lc_job), offsetof(lc_job, dt),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lc_job), offsetof(lc_job, dt),
              offsetof(lc_job, psd), offsetof(lc_job, erdf), offsetof(lc_job, seed),
-             offsetof(lc_job, curve_id), sizeof(lc_erdf), offsetof(lc_erdf, linear_space), sizeof(lc_psd));
+             offsetof(lc_job, curve_id), sizeof(lc_erdf), offsetof(lc_erdf, linear_space),
+             offsetof(lc_erdf, kind), offsetof(lc_erdf, sigma), sizeof(lc_psd));
       return 0;
     }
     """
@@ -62,7 +63,8 @@ def test_struct_layout_matches_c():
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     J, E, P = _abi.LcJob, _abi.LcErdf, _abi.LcPsd
     assert vals == [ctypes.sizeof(J), J.dt.offset, J.psd.offset, J.erdf.offset, J.seed.offset,
-                    J.curve_id.offset, ctypes.sizeof(E), E.linear_space.offset, ctypes.sizeof(P)]
+                    J.curve_id.offset, ctypes.sizeof(E), E.linear_space.offset, E.kind.offset, E.sigma.offset,
+                    ctypes.sizeof(P)]
 
 
 def test_status_strings():
@@ -73,7 +75,10 @@ def test_status_strings():
 
 @pytest.mark.parametrize("bad", [dict(log2n=3), dict(log2n=28), dict(dt=0.0), dict(f_br=-1.0),
                                  dict(log_lbreak=0.5), dict(log_lmin=0.0), dict(alpha_high=float("nan")),
-                                 dict(slope_low=float("inf"))])
+                                 dict(slope_low=float("inf")), dict(erdf_kind=3), dict(erdf_kind=-1),
+                                 dict(erdf_kind=2, sigma=0.0), dict(erdf_kind=2, sigma=0.001),
+                                 dict(erdf_kind=2, sigma=0.5, log_lbreak=-40.0),
+                                 dict(erdf_kind=1, log_lbreak=0.5)])
 def test_invalid_jobs_are_rejected_before_any_device_work(bad):
     j = workloads.job(10, 3, 0, 0)
     j.update(bad)
@@ -90,3 +95,4 @@ def test_null_arguments_are_rejected():
     assert lib.lc_plan_destroy(None) == _abi.LC_ERR_INVALID
     assert lib.lc_iterate(None, 1, None) == _abi.LC_ERR_INVALID
     assert lib.lc_poll(None, 0, None, None) != _abi.LC_OK
+

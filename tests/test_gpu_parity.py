@@ -37,6 +37,16 @@ JOBSETS = {
     "ragged_2^4..2^14": lambda: small_ragged(),
     "long_2^20": lambda: workloads.long_curves(ncurves=2, log2n=20, iters=2),
     "linear_space": lambda: [workloads.job(11, 2, seed=5, curve_id=9, linear_space=1)],
+    # the tabulated ERDF shapes (Eq. 1 smooth, Eq. 2 log-normal), mixed with a
+    # sharp curve, on the fused (2^12) and multi-kernel (2^9, 2^17) paths
+    "erdf_shapes": lambda: [
+        workloads.job(12, 3, seed=21, curve_id=0, **workloads.ERDF_SHAPES["smooth_eq1"]),
+        workloads.job(12, 3, seed=22, curve_id=1, **workloads.ERDF_SHAPES["lognormal"]),
+        workloads.job(12, 3, seed=23, curve_id=2),
+        workloads.job(9, 3, seed=24, curve_id=3, **workloads.ERDF_SHAPES["table2"]),
+        workloads.job(17, 2, seed=25, curve_id=4, linear_space=1, **workloads.ERDF_SHAPES["lognormal"]),
+        workloads.job(10, 3, seed=26, curve_id=5, linear_space=1, **workloads.ERDF_SHAPES["table2"]),
+    ],
 }
 
 
@@ -52,7 +62,8 @@ def test_draws_bit_exact_and_sorted(name, prec):
     for c, j in enumerate(jobs):
         n = 1 << j["log2n"]
         erdf = oracle.job_params(j)[4:]
-        d = oracle.erdf_draws(erdf, n, j["seed"], j["curve_id"], prec=po, linear_space=j.get("linear_space", 0))
+        d = oracle.erdf_draws(erdf, n, j["seed"], j["curve_id"], prec=po, linear_space=j.get("linear_space", 0),
+                              kind=j.get("erdf_kind", 0))
         seg = slice(p.offsets[c], p.offsets[c + 1])
         assert np.array_equal(x0[seg], d), (name, c)
         assert np.array_equal(s[seg], np.sort(d)), (name, c)

@@ -34,6 +34,11 @@ def _mixed_jobs(n, seed):
                                   curve_id=c, f_br=float(10 ** rng.uniform(-4, -1)),
                                   alpha_high=float(rng.uniform(2, 3)), log_lbreak=float(rng.uniform(-2.5, -0.5)),
                                   slope_high=float(rng.uniform(-3, -1.5))))
+    # the tabulated ERDF shapes (Eq. 1 smooth, Eq. 2 log-normal) run in the same cohorts
+    shapes = list(workloads.ERDF_SHAPES.values())
+    for c in range(0, n, 5):
+        jobs[c] = workloads.job(jobs[c]["log2n"], jobs[c]["iters"], seed=jobs[c]["seed"], curve_id=c,
+                                **shapes[(c // 5) % len(shapes)])
     return jobs
 
 

@@ -17,7 +17,9 @@ def test_noalloc_matches_lc_generate_on_consecutive_calls():
     lib = _abi.load()
     jobs = [workloads.job(12, 10, seed=7, curve_id=3),
             workloads.job(16, 4, seed=8, curve_id=4, f_br=0.01, alpha_high=2.6),
-            workloads.job(9, 6, seed=9, curve_id=5, log_lbreak=-2.0, slope_high=-1.8)]
+            workloads.job(9, 6, seed=9, curve_id=5, log_lbreak=-2.0, slope_high=-1.8),
+            workloads.job(13, 5, seed=10, curve_id=6, **workloads.ERDF_SHAPES["lognormal"]),
+            workloads.job(16, 2, seed=11, curve_id=7, **workloads.ERDF_SHAPES["table2"])]
     stream = torch.cuda.current_stream()
     for j in jobs:
         n = 1 << j["log2n"]
