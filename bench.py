@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--workload", default="uniform", choices=["uniform", "single", "long", "ragged", "serving"],
                     help="uniform (default) is the benchmark line; the others are the remaining workloads")
     ap.add_argument("--serving-seconds", type=float, default=60.0)
+    ap.add_argument("--erdf", default=None, choices=["smooth_eq1", "table2", "lognormal"],
+                    help="give every curve of the uniform workload this tabulated ERDF shape (Eq. 1 / Eq. 2); "
+                         "a variant line, not the bench workload")
     ap.add_argument("--convergence", type=float, default=None, metavar="THRESHOLD",
                     help="run with the Eq. 4 convergence test on (every curve stops once delta < THRESHOLD; "
                          "0 = measure delta without stopping); a variant line, not the bench workload")
@@ -215,6 +218,9 @@ def run_gpu(args):
     samples = workloads.total_samples(jobs)
     sample_iters = workloads.sample_iters(jobs)
     esize = 4 if prec == LC_FP32 else 8
+    if args.erdf is not None:
+        jobs = [dict(j, **workloads.ERDF_SHAPES[args.erdf]) for j in jobs]
+        desc += f"; ERDF shape {args.erdf} (tabulated CDF)"
     plan = Plan(jobs, prec, device=local)
     if args.convergence is not None:
         plan.set_convergence([args.convergence] * len(jobs))
@@ -286,13 +292,14 @@ def run_gpu(args):
 
     peak, peak_kind = measured_peaks()
     it_ms = statistics.median(iter_ms)
+    setup_ms = lc_plan_timing(plan.handle)[0]
     alg_per = ALG_BYTES_PER_SAMPLE_ITER * (2 if prec != LC_FP32 else 1)
     alg_bytes = alg_per * sample_iters
     achieved = alg_bytes / (it_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "kernel": "iteration stage (all E13 iterations of the batch)",
             "peak_kind": peak_kind, "alg_bytes_per_sample_iter": alg_per,
-            "iterate_ms": it_ms}
+            "iterate_ms": it_ms, "setup_ms": setup_ms}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and args.workload == "uniform":
