@@ -60,19 +60,19 @@ def lib():
                 "or_erdf_table": (None, [P, i32, i32, P]),
                 "or_erdf_icdf_tab": (d, [P, P, d]),
                 "or_psd": (d, [d, d, d, d]),
-                "or_tk_spectrum": (None, [u32, d, P, u64, u64, P]),
+                "or_tk_spectrum": (None, [u32, d, P, i32, u64, u64, P]),
                 "or_dft": (None, [sz, P, P, i32]),
                 "or_fft": (None, [sz, P, P, i32]),
                 "or_r2c": (None, [sz, P, P]),
                 "or_c2r": (None, [sz, P, P]),
-                "or_tk_series": (None, [u32, d, P, u64, u64, P, P, P]),
+                "or_tk_series": (None, [u32, d, P, i32, i32, u64, u64, P, P, P]),
                 "or_argsort": (None, [sz, P, P]),
                 "or_sort": (None, [sz, P]),
                 "or_iterate": (None, [u32, P, P, P, u32, P, P]),
                 "or_delta": (d, [sz, P, P]),
                 "or_iterate_conv": (u32, [u32, P, P, P, u32, d, P]),
-                "or_generate": (None, [u32, P, i32, i32, u32, u64, u64, i32, P, P, P, P]),
-                "or_generate_batch": (i32, [sz, P, P, P, P, P, P, P, i32, i32, P]),
+                "or_generate": (None, [u32, P, P, u32, u64, u64, i32, P, P, P, P]),
+                "or_generate_batch": (i32, [sz, P, P, P, P, P, P, i32, i32, P]),
                 "or_spec_exp_v": (None, [sz, P, P]),
                 "or_spec_log_v": (None, [sz, P, P]),
                 "or_spec_log1p_v": (None, [sz, P, P]),
@@ -170,10 +170,11 @@ def psd(f, f_br, a_low, a_high):
     return lib().or_psd(float(f), float(f_br), float(a_low), float(a_high))
 
 
-def tk_spectrum(log2n, dt, psd_params, seed, curve_id) -> np.ndarray:
+def tk_spectrum(log2n, dt, psd_params, seed, curve_id, coeffs=0) -> np.ndarray:
+    """coeffs 0: TK95 Gaussian coefficients; 1: fixed amplitude sqrt(P), random phase."""
     n = 1 << log2n
     ps = _f64(psd_params); X = np.empty(2 * (n // 2 + 1), dtype=np.float64)
-    lib().or_tk_spectrum(log2n, dt, _p(ps), seed, curve_id, _p(X))
+    lib().or_tk_spectrum(log2n, dt, _p(ps), int(coeffs), seed, curve_id, _p(X))
     return X[0::2] + 1j * X[1::2]
 
 
@@ -197,12 +198,13 @@ def c2r(Y, n):
     lib().or_c2r(n, _p(Y), _p(out)); return out
 
 
-def tk_series(log2n, dt, psd_params, seed, curve_id):
-    """Normalised TK95 series, target amplitudes A (n/2+1) and sigma."""
+def tk_series(log2n, dt, psd_params, seed, curve_id, coeffs=0, targets=0):
+    """Normalised TK95 series, target amplitudes A (n/2+1) and sigma
+    (targets 1: the amplitudes of the PSD itself)."""
     n = 1 << log2n
     ps = _f64(psd_params)
     x = np.empty(n); A = np.empty(n // 2 + 1); sig = np.empty(1)
-    lib().or_tk_series(log2n, dt, _p(ps), seed, curve_id, _p(x), _p(A), _p(sig))
+    lib().or_tk_series(log2n, dt, _p(ps), int(coeffs), int(targets), seed, curve_id, _p(x), _p(A), _p(sig))
     return x, A, float(sig[0])
 
 
@@ -240,6 +242,12 @@ def iterate_conv(A, s, x, iters, thr=0.0):
     return x, d[:run], run
 
 
+def job_modes(job) -> np.ndarray:
+    """{linear_space, ERDF kind, TK coefficients, target amplitudes} of a job dict."""
+    return np.array([job.get("linear_space", 0), job.get("erdf_kind", 0), job.get("tk_coeffs", 0),
+                     job.get("tk_targets", 0)], dtype=np.int32)
+
+
 def job_params(job) -> np.ndarray:
     """Flatten a job dict into the oracle's 10-double parameter block."""
     return np.array([job["dt"], job["f_br"], job["alpha_low"], job["alpha_high"],
@@ -253,8 +261,8 @@ def generate(job, prec=0, want=("x",)):
     log2n = int(job["log2n"]); n = 1 << log2n
     par = job_params(job)
     out = {k: (np.empty(n // 2 + 1) if k == "A" else np.empty(n)) for k in ("x", "tk", "A", "s")}
-    lib().or_generate(log2n, _p(par), int(job.get("linear_space", 0)), int(job.get("erdf_kind", 0)),
-                      int(job["iters"]),
+    modes = job_modes(job)
+    lib().or_generate(log2n, _p(par), _p(modes), int(job["iters"]),
                       int(job["seed"]), int(job["curve_id"]), prec, _p(out["x"]),
                       _p(out["tk"]) if "tk" in want else None,
                       _p(out["A"]) if "A" in want else None,
@@ -267,13 +275,12 @@ def generate_batch(jobs, prec=0, nthreads=1):
     nc = len(jobs)
     log2n = np.array([j["log2n"] for j in jobs], dtype=np.uint32)
     par = np.ascontiguousarray(np.stack([job_params(j) for j in jobs]))
-    lin = np.array([j.get("linear_space", 0) for j in jobs], dtype=np.int32)
-    kind = np.array([j.get("erdf_kind", 0) for j in jobs], dtype=np.int32)
+    modes = np.ascontiguousarray(np.stack([job_modes(j) for j in jobs]))
     iters = np.array([j["iters"] for j in jobs], dtype=np.uint32)
     seed = np.array([j["seed"] for j in jobs], dtype=np.uint64)
     cid = np.array([j["curve_id"] for j in jobs], dtype=np.uint64)
     total = int(sum(1 << int(l) for l in log2n))
     out = np.empty(total)
-    used = lib().or_generate_batch(nc, _p(log2n), _p(par), _p(lin), _p(kind), _p(iters), _p(seed),
+    used = lib().or_generate_batch(nc, _p(log2n), _p(par), _p(modes), _p(iters), _p(seed),
                                    _p(cid), prec, int(nthreads), _p(out))
     return out, int(used)

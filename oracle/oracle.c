@@ -353,8 +353,11 @@ OR_API double or_psd(double f, double f_br, double a_low, double a_high)
  * (App. A), X_0 = 0, X_j = sqrt(P_j/2) (g_re + i g_im) for 0 < j < N/2 and the
  * real Nyquist bin X_{N/2} = sqrt(P_{N/2}) g_re.  The Gaussians come from Box-
  * Muller on the two uniforms of Philox block j of stream 0.
+ * coeffs = 1 is the fixed-amplitude variant: X_j = sqrt(P_j) e^{2 pi i U2}
+ * (same mean power, no scatter of |X_j|) and X_{N/2} = +-sqrt(P_{N/2}) with
+ * the sign of cos(2 pi U2).
  * X has 2*(N/2+1) doubles (re, im interleaved). */
-OR_API void or_tk_spectrum(uint32_t log2n, double dt, const double psd[3],
+OR_API void or_tk_spectrum(uint32_t log2n, double dt, const double psd[3], int coeffs,
                            uint64_t seed, uint64_t curve_id, double* X)
 {
     size_t n = (size_t)1 << log2n, nh = n / 2;
@@ -364,16 +367,16 @@ OR_API void or_tk_spectrum(uint32_t log2n, double dt, const double psd[3],
         uint32_t w[4];
         philox_block(seed, curve_id, 0u, (uint64_t)j, w);
         double U1 = or_u01(w[0], w[1]), U2 = or_u01(w[2], w[3]);
-        double rad = sqrt(-2.0 * log(U1));
+        double rad = coeffs == 1 ? 1.0 : sqrt(-2.0 * log(U1));
         double g_re = rad * cos(two_pi * U2), g_im = rad * sin(two_pi * U2);
         double f = (double)j / ((double)n * dt);
         double P = or_psd(f, psd[0], psd[1], psd[2]);
         if (j < nh) {
-            double a = sqrt(P / 2.0);
+            double a = coeffs == 1 ? sqrt(P) : sqrt(P / 2.0);
             X[2 * j] = a * g_re;
             X[2 * j + 1] = a * g_im;
         } else {
-            X[2 * j] = sqrt(P) * g_re;
+            X[2 * j] = coeffs == 1 ? (g_re < 0.0 ? -sqrt(P) : sqrt(P)) : sqrt(P) * g_re;
             X[2 * j + 1] = 0.0;
         }
     }
@@ -467,13 +470,16 @@ OR_API void or_c2r(size_t n, const double* Y, double* x)
 /* TK95 series and target amplitudes (Sec. 2.1 first step; normalised E13   */
 /* series): x = C2R(X), mu = mean, sigma^2 = population variance,           */
 /* x_TK = (x - mu)/sigma, A_j = |X_j|/sigma with A_0 = 0.                    */
+/* targets = 1 takes the amplitudes from the PSD itself instead of the       */
+/* realisation: A_j = sqrt(P_j)/sigma_P with sigma_P^2 = P_{N/2} +           */
+/* 2 sum_{0<j<N/2} P_j, the series variance that the PSD implies.           */
 /* ------------------------------------------------------------------------ */
-OR_API void or_tk_series(uint32_t log2n, double dt, const double psd[3], uint64_t seed,
-                         uint64_t curve_id, double* x_tk, double* A, double* sigma_out)
+OR_API void or_tk_series(uint32_t log2n, double dt, const double psd[3], int coeffs, int targets,
+                         uint64_t seed, uint64_t curve_id, double* x_tk, double* A, double* sigma_out)
 {
     size_t n = (size_t)1 << log2n, nh = n / 2;
     double* X = (double*)malloc(sizeof(double) * 2 * (nh + 1));
-    or_tk_spectrum(log2n, dt, psd, seed, curve_id, X);
+    or_tk_spectrum(log2n, dt, psd, coeffs, seed, curve_id, X);
     or_c2r(n, X, x_tk);
     double mu = 0.0;
     for (size_t k = 0; k < n; ++k) mu += x_tk[k];
@@ -484,7 +490,18 @@ OR_API void or_tk_series(uint32_t log2n, double dt, const double psd[3], uint64_
     double sigma = sqrt(var);
     for (size_t k = 0; k < n; ++k) x_tk[k] = (x_tk[k] - mu) / sigma;
     A[0] = 0.0;
-    for (size_t j = 1; j <= nh; ++j) A[j] = hypot(X[2 * j], X[2 * j + 1]) / sigma;
+    if (targets == 1) {
+        double sp = 0.0;
+        for (size_t j = 1; j <= nh; ++j) {
+            double P = or_psd((double)j / ((double)n * dt), psd[0], psd[1], psd[2]);
+            sp += j < nh ? 2.0 * P : P;
+        }
+        double sigma_p = sqrt(sp);
+        for (size_t j = 1; j <= nh; ++j)
+            A[j] = sqrt(or_psd((double)j / ((double)n * dt), psd[0], psd[1], psd[2])) / sigma_p;
+    } else {
+        for (size_t j = 1; j <= nh; ++j) A[j] = hypot(X[2 * j], X[2 * j + 1]) / sigma;
+    }
     if (sigma_out) *sigma_out = sigma;
     free(X);
 }
@@ -608,13 +625,15 @@ OR_API uint32_t or_iterate_conv(uint32_t log2n, const double* A, const double* s
 
 /* ------------------------------------------------------------------------ */
 /* Whole generator for one curve.  params[] = {dt, f_br, a_low, a_high,      */
-/* log_lmin, log_lmax, log_lbreak, slope_low, slope_high, sigma}; kind is    */
-/* the ERDF shape (0 sharp, 1 smooth Eq. 1, 2 log-normal Eq. 2).             */
+/* log_lmin, log_lmax, log_lbreak, slope_low, slope_high, sigma};           */
+/* modes[] = {linear_space, ERDF kind (0 sharp, 1 smooth Eq. 1, 2 log-normal */
+/* Eq. 2), TK coefficients (0 Gaussian, 1 fixed amplitude), targets (0 the   */
+/* realised amplitudes, 1 those of the PSD)}.                               */
 /* out_x (n) receives the final series; out_tk (n, nullable) the normalised   */
 /* TK95 series; out_A (n/2+1, nullable) the amplitudes; out_s (n, nullable)  */
 /* the sorted draws.  prec 0 = draws rounded to float, 1 = double.          */
 /* ------------------------------------------------------------------------ */
-OR_API void or_generate(uint32_t log2n, const double params[10], int linear_space, int kind,
+OR_API void or_generate(uint32_t log2n, const double params[10], const int modes[4],
                         uint32_t iters, uint64_t seed, uint64_t curve_id, int prec,
                         double* out_x, double* out_tk, double* out_A, double* out_s)
 {
@@ -624,8 +643,8 @@ OR_API void or_generate(uint32_t log2n, const double params[10], int linear_spac
     double* xtk = (double*)malloc(sizeof(double) * n);
     double* A = (double*)malloc(sizeof(double) * (nh + 1));
     double* s = (double*)malloc(sizeof(double) * n);
-    or_tk_series(log2n, params[0], psd, seed, curve_id, xtk, A, NULL);
-    or_erdf_draws(erdf, linear_space, kind, seed, curve_id, prec, n, out_x);
+    or_tk_series(log2n, params[0], psd, modes[2], modes[3], seed, curve_id, xtk, A, NULL);
+    or_erdf_draws(erdf, modes[0], modes[1], seed, curve_id, prec, n, out_x);
     memcpy(s, out_x, sizeof(double) * n);
     or_sort(n, s);
     or_iterate(log2n, A, s, out_x, iters, NULL, NULL);
@@ -638,12 +657,12 @@ OR_API void or_generate(uint32_t log2n, const double params[10], int linear_spac
 /* ------------------------------------------------------------------------ */
 /* A batch of independent curves on `nthreads` host threads (curves are      */
 /* independent, so this is only a loop split across threads).               */
-/* log2n[c], params[10c..10c+9], linear_space[c], kind[c], iters[c],       */
-/* seed[c], curve_id[c]; out_x is the concatenation of the curves in order. */
+/* log2n[c], params[10c..10c+9], modes[4c..4c+3], iters[c], seed[c],       */
+/* curve_id[c]; out_x is the concatenation of the curves in order.          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     size_t ncurves;
-    const uint32_t* log2n; const double* params; const int* lin; const int* kind; const uint32_t* iters;
+    const uint32_t* log2n; const double* params; const int* modes; const uint32_t* iters;
     const uint64_t* seed; const uint64_t* curve_id; int prec;
     double* out_x; const size_t* offsets;
     size_t next; pthread_mutex_t lock;
@@ -657,21 +676,21 @@ static void* batch_worker(void* arg)
         size_t c = b->next++;
         pthread_mutex_unlock(&b->lock);
         if (c >= b->ncurves) break;
-        or_generate(b->log2n[c], b->params + 10 * c, b->lin[c], b->kind[c], b->iters[c], b->seed[c],
+        or_generate(b->log2n[c], b->params + 10 * c, b->modes + 4 * c, b->iters[c], b->seed[c],
                     b->curve_id[c], b->prec, b->out_x + b->offsets[c], NULL, NULL, NULL);
     }
     return NULL;
 }
 
 OR_API int or_generate_batch(size_t ncurves, const uint32_t* log2n, const double* params,
-                             const int* linear_space, const int* kind, const uint32_t* iters,
+                             const int* modes, const uint32_t* iters,
                              const uint64_t* seed, const uint64_t* curve_id, int prec,
                              int nthreads, double* out_x)
 {
     size_t* offsets = (size_t*)malloc(sizeof(size_t) * (ncurves + 1));
     offsets[0] = 0;
     for (size_t c = 0; c < ncurves; ++c) offsets[c + 1] = offsets[c] + ((size_t)1 << log2n[c]);
-    batch_ctx b = {ncurves, log2n, params, linear_space, kind, iters, seed, curve_id, prec,
+    batch_ctx b = {ncurves, log2n, params, modes, iters, seed, curve_id, prec,
                    out_x, offsets, 0, PTHREAD_MUTEX_INITIALIZER};
     if (nthreads < 1) nthreads = 1;
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);

@@ -82,7 +82,8 @@ def test_tk_stage_and_amplitudes(name, prec):
     for c, j in enumerate(jobs):
         n = 1 << j["log2n"]
         par = oracle.job_params(j)
-        x_tk, A_or, _ = oracle.tk_series(j["log2n"], par[0], par[1:4], j["seed"], j["curve_id"])
+        x_tk, A_or, _ = oracle.tk_series(j["log2n"], par[0], par[1:4], j["seed"], j["curve_id"],
+                                         coeffs=j.get("tk_coeffs", 0), targets=j.get("tk_targets", 0))
         err = rel_l2(tk[p.offsets[c]:p.offsets[c + 1]], x_tk)
         assert err <= (TK_TOL if prec == LC_FP32 else 1e-12), (name, c, err)
         a = A[offh:offh + n // 2 + 1]

@@ -626,3 +626,52 @@ def _cdf_table_smooth(e):
     f = 1.0 / (r ** w["delta1"] + r ** w["delta2"])
     c = np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(u))])
     return u, c / c[-1]
+
+
+# ------------------------------------------------ PSD variants (Sec. 3.1, Sec. 2.1)
+def test_eq3_with_equal_slopes_is_a_single_power_law():
+    """Sec. 3.1 names single and broken power-law PSDs: Eq. 3 with
+    alpha_low = alpha_high = alpha is (f/f_br)^-alpha / 2 exactly."""
+    for a in (1.0, 1.7, 2.5):
+        for f in (1e-6, 3.3e-3, 0.4, 17.0):
+            assert oracle.psd(f, 1 / 300.0, a, a) == pytest.approx(0.5 * (f * 300.0) ** -a, rel=1e-14)
+
+
+def test_fixed_amplitude_coefficients():
+    """The fixed-amplitude variant: |X_j|^2 = P_j (the Gaussian mode's mean
+    power, without its scatter), the same phases as the Gaussian mode (same
+    Philox words), phases uniform; the Nyquist bin is +-sqrt(P_{N/2})."""
+    log2n, dt = 12, 1.0
+    n = 1 << log2n
+    Xg = oracle.tk_spectrum(log2n, dt, PSD_BASE, 5, 3, coeffs=0)
+    Xf = oracle.tk_spectrum(log2n, dt, PSD_BASE, 5, 3, coeffs=1)
+    j = np.arange(1, n // 2)
+    P = np.array([oracle.psd(v / (n * dt), *PSD_BASE) for v in j])
+    np.testing.assert_allclose(np.abs(Xf[1:n // 2]) ** 2, P, rtol=1e-13)
+    np.testing.assert_allclose(Xf[1:n // 2] / np.abs(Xf[1:n // 2]), Xg[1:n // 2] / np.abs(Xg[1:n // 2]),
+                               rtol=0, atol=1e-13)
+    PM = oracle.psd(0.5 / dt, *PSD_BASE)
+    assert Xf[0] == 0 and Xf[-1].imag == 0 and abs(Xf[-1].real) == pytest.approx(math.sqrt(PM), rel=1e-15)
+    assert np.sign(Xf[-1].real) == (np.sign(Xg[-1].real) or 1.0)
+    phi = np.sort(np.mod(np.angle(Xf[1:n // 2]) / (2 * np.pi), 1.0))
+    emp = np.arange(1, phi.size + 1) / phi.size
+    assert np.max(np.abs(emp - phi)) < 1.95 / math.sqrt(phi.size)
+
+
+@pytest.mark.parametrize("coeffs,targets", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_target_amplitudes_normalisation(coeffs, targets):
+    """Either way A_0 = 0 and A_{N/2}^2 + 2 sum A_j^2 = 1 (the normalised
+    series has unit variance, Parseval); with PSD targets A_j^2 is P_j times
+    one constant, whatever the realisation."""
+    log2n = 11
+    n = 1 << log2n
+    x, A, _ = oracle.tk_series(log2n, 1.0, PSD_BASE, 9, 2, coeffs=coeffs, targets=targets)
+    assert A[0] == 0.0
+    assert A[-1] ** 2 + 2 * np.sum(A[1:-1] ** 2) == pytest.approx(1.0, rel=1e-12)
+    assert np.mean(x) == pytest.approx(0.0, abs=1e-12) and np.var(x) == pytest.approx(1.0, rel=1e-12)
+    if targets == 1:
+        P = np.array([oracle.psd(v / n, *PSD_BASE) for v in range(1, n // 2 + 1)])
+        r = A[1:] ** 2 / P
+        np.testing.assert_allclose(r, r[0], rtol=1e-13)
+        _, A_other, _ = oracle.tk_series(log2n, 1.0, PSD_BASE, 10, 7, coeffs=coeffs, targets=1)
+        np.testing.assert_array_equal(A, A_other)
