@@ -70,6 +70,8 @@ def lib():
                 "or_sort": (None, [sz, P]),
                 "or_iterate": (None, [u32, P, P, P, u32, P, P]),
                 "or_delta": (d, [sz, P, P]),
+                "or_periodogram": (None, [sz, P, d, i32, P]),
+                "or_structure_function": (None, [sz, P, sz, P, P]),
                 "or_iterate_conv": (u32, [u32, P, P, P, u32, d, P]),
                 "or_generate": (None, [u32, P, P, u32, u64, u64, i32, P, P, P, P]),
                 "or_generate_batch": (i32, [sz, P, P, P, P, P, P, i32, i32, P]),
@@ -240,6 +242,18 @@ def iterate_conv(A, s, x, iters, thr=0.0):
     d = np.full(max(int(iters), 1), np.nan)
     run = int(lib().or_iterate_conv(log2n, _p(A), _p(s), _p(x), int(iters), float(thr), _p(d)))
     return x, d[:run], run
+
+
+def periodogram(x, dt=1.0, rms=False):
+    """Eq. A2 (or the rms-normalised Eq. A4) at j = 0..N/2."""
+    x = _f64(x); P = np.empty(x.size // 2 + 1)
+    lib().or_periodogram(x.size, _p(x), float(dt), int(bool(rms)), _p(P)); return P
+
+
+def structure_function(x, lags):
+    """Eq. A6: SF(tau)^2 at integer lags (samples)."""
+    x = _f64(x); L = np.ascontiguousarray(lags, dtype=np.uint32); out = np.empty(L.size)
+    lib().or_structure_function(x.size, _p(x), L.size, _p(L), _p(out)); return out
 
 
 def job_modes(job) -> np.ndarray:

@@ -655,6 +655,45 @@ OR_API void or_generate(uint32_t log2n, const double params[10], const int modes
 }
 
 /* ------------------------------------------------------------------------ */
+/* Periodogram (App. A, Eq. A2): P_j = (2/N^2) |DFT_j|^2 for j = 0..N/2 (the   */
+/* sign of the exponent in Eq. A1 does not change |DFT_j|).  rms = 1 gives the */
+/* fractional rms normalisation of Eq. A4: P_j = 2 dt |DFT_j|^2 / (mu^2 N),    */
+/* mu the mean of the series.  P has N/2+1 entries.                          */
+/* ------------------------------------------------------------------------ */
+OR_API void or_periodogram(size_t n, const double* x, double dt, int rms, double* P)
+{
+    size_t nh = n / 2;
+    double* X = (double*)malloc(sizeof(double) * 2 * (nh + 1));
+    or_r2c(n, x, X);
+    double mu = 0.0;
+    for (size_t k = 0; k < n; ++k) mu += x[k];
+    mu /= (double)n;
+    double nd = (double)n;
+    for (size_t j = 0; j <= nh; ++j) {
+        double p2 = X[2 * j] * X[2 * j] + X[2 * j + 1] * X[2 * j + 1];
+        P[j] = rms ? 2.0 * dt * p2 / (mu * mu * nd) : 2.0 * p2 / (nd * nd);
+    }
+    free(X);
+}
+
+/* Structure function (App. A, Eq. A6) at integer lags tau (in samples):     */
+/* SF(tau)^2 = (1/P) sum over the P = N - tau pairs (x_i, x_{i+tau}) of       */
+/* (x_i - x_{i+tau})^2.  Lags must satisfy 1 <= tau < N.                     */
+OR_API void or_structure_function(size_t n, const double* x, size_t nlags, const uint32_t* lags,
+                                  double* sf2)
+{
+    for (size_t l = 0; l < nlags; ++l) {
+        size_t tau = lags[l];
+        double acc = 0.0;
+        for (size_t i = 0; i + tau < n; ++i) {
+            double d = x[i] - x[i + tau];
+            acc += d * d;
+        }
+        sf2[l] = acc / (double)(n - tau);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* A batch of independent curves on `nthreads` host threads (curves are      */
 /* independent, so this is only a loop split across threads).               */
 /* log2n[c], params[10c..10c+9], modes[4c..4c+3], iters[c], seed[c],       */

@@ -675,3 +675,68 @@ def test_target_amplitudes_normalisation(coeffs, targets):
         np.testing.assert_allclose(r, r[0], rtol=1e-13)
         _, A_other, _ = oracle.tk_series(log2n, 1.0, PSD_BASE, 10, 7, coeffs=coeffs, targets=1)
         np.testing.assert_array_equal(A, A_other)
+
+
+# ------------------------------------- periodogram and structure function (App. A)
+def test_periodogram_closed_forms_and_parseval():
+    """Eq. A2: a cosine of frequency j0 has P_j0 = 1/2 and nothing elsewhere; a
+    constant c has P_0 = 2 c^2; and the half spectrum satisfies
+    P_0 + P_{N/2} + 2 sum_{0<j<N/2} P_j = (2/N) sum x^2 (Parseval)."""
+    n = 256
+    k = np.arange(n)
+    P = oracle.periodogram(np.cos(2 * np.pi * 17 * k / n))
+    assert P[17] == pytest.approx(0.5, rel=1e-13)
+    assert np.max(np.delete(P, 17)) < 1e-25
+    P = oracle.periodogram(np.full(n, 3.0))
+    assert P[0] == pytest.approx(18.0, rel=1e-14) and np.max(P[1:]) < 1e-25
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(n) + 2.0
+    P = oracle.periodogram(x)
+    assert P[0] + P[-1] + 2 * P[1:-1].sum() == pytest.approx(2.0 / n * np.sum(x ** 2), rel=1e-13)
+    # |DFT| against numpy's transform (either sign convention)
+    np.testing.assert_allclose(P, 2.0 / n ** 2 * np.abs(np.fft.rfft(x)) ** 2, rtol=1e-12)
+
+
+def test_rms_periodogram_integrates_to_the_fractional_variance():
+    """Eq. A5: with the rms normalisation of Eq. A4, the sum over
+    f_1..f_{N/2} with df = 1/(N dt), the Nyquist bin weighted 1/2, is
+    exactly sigma^2/mu^2."""
+    n, dt = 1024, 3.5
+    rng = np.random.default_rng(8)
+    x = 10.0 ** rng.uniform(-3, 0, n)
+    P = oracle.periodogram(x, dt=dt, rms=True)
+    df = 1.0 / (n * dt)
+    integral = (P[1:-1].sum() + 0.5 * P[-1]) * df
+    assert integral == pytest.approx(np.var(x) / np.mean(x) ** 2, rel=1e-12)
+    assert P[0] == pytest.approx(2.0 * dt * n, rel=1e-12)  # |DFT_0| = N mu
+
+
+def test_structure_function_closed_forms():
+    """Eq. A6: a ramp a + b t has SF(tau)^2 = b^2 tau^2 at every lag; a series
+    of period p has SF(p) = 0; white noise has SF^2 = 2 sigma^2 (statistical)."""
+    n = 4096
+    k = np.arange(n, dtype=np.float64)
+    lags = np.array([1, 2, 7, 100, 1000, 4095])
+    np.testing.assert_allclose(oracle.structure_function(0.25 + 1.5 * k, lags), (1.5 * lags) ** 2, rtol=1e-14)
+    sq = np.tile(np.sin(2 * np.pi * np.arange(64) / 64.0) ** 3, n // 64)
+    sf = oracle.structure_function(sq, [64, 128, 32])
+    assert sf[0] == 0.0 and sf[1] == 0.0 and sf[2] > 0.1
+    rng = np.random.default_rng(4)
+    w = rng.standard_normal(1 << 16)
+    sf = oracle.structure_function(w, [1, 10, 1000])
+    np.testing.assert_allclose(sf, 2.0, rtol=0.03)
+
+
+def test_structure_function_slope_follows_the_psd_slope():
+    """Sec. A: a power-law PSD with slope -alpha, 1 < alpha < 3, gives an SF
+    slope beta = (alpha - 1)/2 (Wiener-Khinchin).  TK95 realisations of a
+    single power law alpha = 2 (Eq. 3, equal slopes) have beta ~ 0.5 at lags
+    well inside the series."""
+    log2n = 16
+    lags = np.array([8, 16, 32, 64, 128])
+    acc = np.zeros(lags.size)
+    for c in range(8):
+        x, _, _ = oracle.tk_series(log2n, 1.0, np.array([1e-6, 2.0, 2.0]), 40 + c, c)
+        acc += oracle.structure_function(x, lags)
+    beta = np.polyfit(np.log(lags), 0.5 * np.log(acc / 8), 1)[0]
+    assert abs(beta - 0.5) < 0.05
