@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--erdf", default=None, choices=["smooth_eq1", "table2", "lognormal"],
                     help="give every curve of the uniform workload this tabulated ERDF shape (Eq. 1 / Eq. 2); "
                          "a variant line, not the bench workload")
+    ap.add_argument("--post", action="store_true",
+                    help="also time the App. A estimators (periodogram, 64-lag structure function) on the output")
     ap.add_argument("--convergence", type=float, default=None, metavar="THRESHOLD",
                     help="run with the Eq. 4 convergence test on (every curve stops once delta < THRESHOLD; "
                          "0 = measure delta without stopping); a variant line, not the bench workload")
@@ -268,6 +270,37 @@ def run_gpu(args):
                 "median_last_delta": float(np.median([d[c, int(r) - 1] for c, r in enumerate(run) if r > 0]))}
     value = world * sample_iters * args.steps / (max_ms / 1000.0)
 
+    post = None
+    if args.post:
+        import numpy as np
+        lags = np.unique(np.logspace(0, np.log2(min(1 << int(j["log2n"]) for j in jobs) - 1), 64,
+                                     base=2).astype(np.uint32))
+        nh = sum((1 << int(j["log2n"])) // 2 + 1 for j in jobs)
+        pbuf = torch.empty(nh, dtype=torch.float64, device="cuda")
+        sbuf = torch.empty((len(jobs), lags.size), dtype=torch.float64, device="cuda")
+        from paper_1909_06374_gb300 import lc_periodogram, lc_structure_function
+        for _ in range(2):
+            lc_periodogram(plan.handle, out, False, pbuf, stream)
+            lc_structure_function(plan.handle, out, lags, sbuf, stream)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            lc_periodogram(plan.handle, out, False, pbuf, stream)
+        e1.record(stream)
+        for _ in range(reps):
+            lc_structure_function(plan.handle, out, lags, sbuf, stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        pm, sm = e0.elapsed_time(e1) / reps, e1.elapsed_time(e2) / reps
+        # algorithmic bytes: the series read once (and the spectrum written) / once per lag
+        pb = samples * esize + nh * 8
+        sb = samples * esize * lags.size
+        post = {"periodogram_ms": pm, "periodogram_gbs": pb / (pm / 1e3) / 1e9,
+                "sf_ms": sm, "sf_lags": int(lags.size), "sf_gbs_one_read_per_lag": sb / (sm / 1e3) / 1e9,
+                "sf_pair_terms_per_s": float(sum(((1 << int(j["log2n"])) - int(l)) for j in jobs for l in lags))
+                / (sm / 1e3)}
+
     # end-to-end through the host entry point: job table in, series out
     e2e = None
     if not args.no_e2e and args.convergence is None:
@@ -322,6 +355,8 @@ def run_gpu(args):
                 "clocks": clk.summary()}
         if conv is not None:
             line["convergence"] = conv
+        if post is not None:
+            line["postproc"] = post
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

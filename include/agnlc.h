@@ -62,11 +62,24 @@ typedef enum { LC_FP32 = 0, LC_FP64 = 1 } lc_precision;
 
 /* PSD of Eq. 3 with A = 1: P(f) = [(f/f_br)^alpha_low + (f/f_br)^alpha_high]^-1.
  * f_br is in inverse units of dt (e.g. day^-1 when dt is in days); the PSD
- * falls as f^-alpha_low below and f^-alpha_high above the break. */
+ * falls as f^-alpha_low below and f^-alpha_high above the break.  Equal
+ * slopes give the single power law (f/f_br)^-alpha / 2 (Sec. 3.1).
+ *   coeffs:  LC_TK_GAUSSIAN (0): TK95 coefficients, Re and Im Gaussian with
+ *            variance P_j/2 (the periodogram scatters around the PSD);
+ *            LC_TK_FIXED_AMPLITUDE (1): |X_j| = sqrt(P_j) with a uniform
+ *            random phase (same mean power, no scatter).
+ *   targets: LC_TARGETS_REALISED (0): the iteration imposes the amplitudes of
+ *            the realised TK series (E13); LC_TARGETS_PSD (1): the amplitudes
+ *            of the PSD itself, sqrt(P_j) normalised to unit variance. */
+typedef enum { LC_TK_GAUSSIAN = 0, LC_TK_FIXED_AMPLITUDE = 1 } lc_tk_coeffs;
+typedef enum { LC_TARGETS_REALISED = 0, LC_TARGETS_PSD = 1 } lc_targets;
+
 typedef struct {
     double f_br;
     double alpha_low;
     double alpha_high;
+    int32_t coeffs;        /* lc_tk_coeffs  */
+    int32_t targets;       /* lc_targets    */
 } lc_psd;
 
 /* Shape of the ERDF (Sec. 2.1.1). */
@@ -222,6 +235,35 @@ LC_API lc_status lc_plan_set_convergence(lc_plan plan, const double* thresholds,
  * curve ran (its job count, or fewer when it stopped).  LC_ERR_INVALID
  * before lc_plan_set_convergence. */
 LC_API lc_status lc_plan_convergence(lc_plan plan, double* deltas, uint32_t* iters_run);
+
+/* ------------------------------------------------------- App. A estimators */
+
+/* Periodogram (App. A, Eq. A2) of every curve of a series laid out like the
+ * plan's state: P_j = (2/N^2) |DFT_j|^2 at f_j = j/(N dt), j = 0..N/2; with
+ * rms != 0 the fractional rms normalisation of Eq. A4,
+ * P_j = 2 dt |DFT_j|^2 / (mu^2 N), mu the curve's mean (a zero-mean curve
+ * then gives inf or NaN).  The transform runs in the plan's precision.
+ *   x:     device pointer, sum_c N_c elements of the plan's type (float for
+ *          LC_FP32, double for LC_FP64), e.g. the out_x of lc_generate; read
+ *          only.
+ *   out_p: device pointer, sum_c (N_c/2+1) doubles, curve c at
+ *          sum_{c'<c} (N_{c'}/2+1) (the layout of the amplitude buffer).
+ * Uses the plan's FFT work buffers, so it is ordered with the plan's other
+ * calls on the plan's stream (asynchronous like lc_generate). */
+LC_API lc_status lc_periodogram(lc_plan plan, const void* x, int rms, double* out_p, void* stream);
+
+/* Structure function (App. A, Eq. A6) of every curve at integer lags:
+ * SF(tau)^2 = the mean over the N - tau pairs (x_i, x_{i+tau}) of
+ * (x_i - x_{i+tau})^2, i.e. time lag tau * dt of the curve.
+ *   x:       device pointer laid out as for lc_periodogram; read only.
+ *   lags:    host array of nlags lags in samples, read during the call;
+ *            1 <= lag < N of the shortest curve and 1 <= nlags <= 4096,
+ *            otherwise LC_ERR_INVALID.
+ *   out_sf2: device pointer, ncurves * nlags doubles, row c (job order)
+ *            holds SF^2 of curve c at each lag.
+ * Sums in FP64 (runs of 64 squares in the plan's precision first). */
+LC_API lc_status lc_structure_function(lc_plan plan, const void* x, const uint32_t* lags, size_t nlags,
+                                double* out_sf2, void* stream);
 
 /* Release the plan and its device memory (synchronises its stream). */
 LC_API lc_status lc_plan_destroy(lc_plan plan);

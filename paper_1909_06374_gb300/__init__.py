@@ -10,7 +10,8 @@ from __future__ import annotations
 
 from . import _abi
 from ._abi import (LC_FP32, LC_FP64, LcError, lc_generate, lc_generate_host, lc_get_state, lc_iterate,
-                   lc_plan_buffer, lc_plan_convergence, lc_plan_create, lc_plan_destroy, lc_plan_last_launches,
+                   lc_periodogram, lc_plan_buffer, lc_plan_convergence, lc_plan_create, lc_plan_destroy,
+                   lc_plan_last_launches, lc_structure_function,
                    lc_plan_set_convergence, lc_plan_timing, lc_plan_total_samples, lc_plan_workspace_bytes,
                    lc_poll, lc_server_create, lc_server_destroy, lc_server_stats, lc_set_state, lc_setup,
                    lc_submit)
@@ -18,7 +19,7 @@ from ._abi import (LC_FP32, LC_FP64, LcError, lc_generate, lc_generate_host, lc_
 __all__ = ["Plan", "LC_FP32", "LC_FP64", "LcError", "lc_plan_create", "lc_generate", "lc_generate_host",
            "lc_setup", "lc_iterate", "lc_get_state", "lc_set_state", "lc_plan_buffer",
            "lc_plan_last_launches", "lc_plan_timing", "lc_plan_total_samples", "lc_plan_workspace_bytes", "lc_plan_destroy",
-           "lc_plan_set_convergence", "lc_plan_convergence",
+           "lc_plan_set_convergence", "lc_plan_convergence", "lc_periodogram", "lc_structure_function",
            "lc_server_create", "lc_submit", "lc_poll", "lc_server_stats", "lc_server_destroy"]
 
 
@@ -87,6 +88,21 @@ class Plan:
     def convergence(self):
         """(deltas [ncurves, history], iters_run [ncurves]) of the last run."""
         return lc_plan_convergence(self.handle, len(self.jobs), self.history)
+
+    def periodogram(self, x, rms=False, stream=None):
+        """Eq. A2 (or Eq. A4) of every curve of x; float64 tensor laid out like A."""
+        import torch
+        nh = sum((1 << int(j["log2n"])) // 2 + 1 for j in self.jobs)
+        out = torch.empty(nh, dtype=torch.float64, device=f"cuda:{self.device}")
+        lc_periodogram(self.handle, x, rms, out, self._stream(stream))
+        return out
+
+    def structure_function(self, x, lags, stream=None):
+        """Eq. A6: SF(tau)^2 of every curve at integer lags; float64 [ncurves, nlags]."""
+        import torch
+        out = torch.empty((len(self.jobs), len(lags)), dtype=torch.float64, device=f"cuda:{self.device}")
+        lc_structure_function(self.handle, x, lags, out, self._stream(stream))
+        return out
 
     def curve(self, x, c):
         return x[self.offsets[c]:self.offsets[c + 1]]

@@ -23,8 +23,12 @@ LC_ERR_INVALID, LC_ERR_NOMEM, LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_BUSY, LC_ERR_U
 LC_FP32, LC_FP64 = 0, 1
 
 
+LC_TK_GAUSSIAN, LC_TK_FIXED_AMPLITUDE = 0, 1
+LC_TARGETS_REALISED, LC_TARGETS_PSD = 0, 1
+
+
 class LcPsd(ctypes.Structure):
-    _fields_ = [("f_br", c_d), ("alpha_low", c_d), ("alpha_high", c_d)]
+    _fields_ = [("f_br", c_d), ("alpha_low", c_d), ("alpha_high", c_d), ("coeffs", c_i32), ("targets", c_i32)]
 
 
 LC_ERDF_SHARP, LC_ERDF_SMOOTH, LC_ERDF_LOGNORMAL = 0, 1, 2
@@ -63,6 +67,8 @@ _SIGS = {
     "lc_plan_timing": (c_i32, [c_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "lc_plan_set_convergence": (c_i32, [c_p, c_p, c_u32]),
     "lc_plan_convergence": (c_i32, [c_p, c_p, c_p]),
+    "lc_periodogram": (c_i32, [c_p, c_p, c_i32, c_p, c_p]),
+    "lc_structure_function": (c_i32, [c_p, c_p, c_p, c_sz, c_p, c_p]),
     "lc_plan_destroy": (c_i32, [c_p]),
     "lc_generate_noalloc": (c_i32, [ctypes.POINTER(LcJob), c_p, c_p]),
     "lc_server_create": (c_i32, [c_i32, c_sz, c_i32, ctypes.POINTER(c_p)]),
@@ -137,7 +143,8 @@ def stream_ptr(s):
 def make_job(j) -> LcJob:
     """LcJob from a job dict (keys as in workloads.job)."""
     return LcJob(int(j["log2n"]), int(j["iters"]), float(j["dt"]),
-                 LcPsd(float(j["f_br"]), float(j["alpha_low"]), float(j["alpha_high"])),
+                 LcPsd(float(j["f_br"]), float(j["alpha_low"]), float(j["alpha_high"]), int(j.get("tk_coeffs", 0)),
+                       int(j.get("tk_targets", 0))),
                  LcErdf(float(j["log_lmin"]), float(j["log_lmax"]), float(j["log_lbreak"]),
                         float(j["slope_low"]), float(j["slope_high"]), int(j.get("linear_space", 0)),
                         int(j.get("erdf_kind", 0)), float(j.get("sigma", 0.0))),
@@ -232,6 +239,17 @@ def lc_plan_convergence(plan, ncurves, history):
     r = np.empty(ncurves, dtype=np.uint32)
     _check(load().lc_plan_convergence(plan, d.ctypes.data_as(c_p), r.ctypes.data_as(c_p)), "lc_plan_convergence")
     return d, r
+
+
+def lc_periodogram(plan, x, rms, out_p, stream=None):
+    _check(load().lc_periodogram(plan, ptr(x), int(bool(rms)), ptr(out_p), stream_ptr(stream)), "lc_periodogram")
+
+
+def lc_structure_function(plan, x, lags, out_sf2, stream=None):
+    import numpy as np
+    L = np.ascontiguousarray(lags, dtype=np.uint32)
+    _check(load().lc_structure_function(plan, ptr(x), L.ctypes.data_as(c_p), L.size, ptr(out_sf2),
+                                        stream_ptr(stream)), "lc_structure_function")
 
 
 def lc_plan_destroy(plan):

@@ -23,27 +23,6 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error_text() { return g_last_error.c_str(); }
 
-#define LC_CK(call)                                                                          \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess) {                                                             \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
-            return LC_ERR_CUDA;                                                              \
-        }                                                                                    \
-    } while (0)
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 __global__ void k_iter_increment(int* d_iter) { ++*d_iter; }
 
@@ -74,6 +53,8 @@ lc_status validate_job(const lc_job& j)
     if (!(j.dt > 0) || !finite(j.dt)) { set_error("dt must be > 0"); return LC_ERR_INVALID; }
     if (!(j.psd.f_br > 0) || !finite(j.psd.f_br)) { set_error("f_br must be > 0"); return LC_ERR_INVALID; }
     if (!finite(j.psd.alpha_low) || !finite(j.psd.alpha_high)) { set_error("PSD slopes must be finite"); return LC_ERR_INVALID; }
+    if (j.psd.coeffs < LC_TK_GAUSSIAN || j.psd.coeffs > LC_TK_FIXED_AMPLITUDE) { set_error("unknown TK coefficient mode"); return LC_ERR_INVALID; }
+    if (j.psd.targets < LC_TARGETS_REALISED || j.psd.targets > LC_TARGETS_PSD) { set_error("unknown target amplitude mode"); return LC_ERR_INVALID; }
     const lc_erdf& e = j.erdf;
     if (e.kind < LC_ERDF_SHARP || e.kind > LC_ERDF_LOGNORMAL) { set_error("unknown ERDF kind"); return LC_ERR_INVALID; }
     if (!finite(e.log_lmin) || !finite(e.log_lmax) || !finite(e.log_lbreak) || !finite(e.slope_low) ||
@@ -105,6 +86,8 @@ CurveDev curve_from_job(const lc_job& j)
     cv.umin = j.erdf.log_lmin; cv.umax = j.erdf.log_lmax; cv.ub = j.erdf.log_lbreak;
     cv.sl_lo = j.erdf.slope_low; cv.sl_hi = j.erdf.slope_high; cv.lin = j.erdf.linear_space ? 1 : 0;
     cv.kind = j.erdf.kind;
+    cv.coeffs = j.psd.coeffs;
+    cv.targets = j.psd.targets;
     cv.sigma = j.erdf.kind == LC_ERDF_LOGNORMAL ? j.erdf.sigma : 0.0;
     cv.seed = j.seed; cv.curve_id = j.curve_id;
     return cv;
@@ -204,10 +187,10 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     auto take = [&](size_t bytes) { size_t o = sz; sz = align_up(sz + bytes, A256); return o; };
     const size_t o_curves = take(sizeof(CurveDev) * njobs);
     const size_t o_erdf = take(sizeof(ErdfConst) * njobs);
-    const size_t o_sigma = take(sizeof(double) * njobs);
+    const size_t o_sigma = take(sizeof(double) * 2 * njobs);  // realised, then PSD
     const size_t o_eff = take(sizeof(uint32_t) * njobs);
     const size_t o_iter = take(sizeof(int) * 4);
-    const size_t o_partial = take(sizeof(double) * partial);
+    const size_t o_partial = take(sizeof(double) * 2 * partial);
     const size_t o_x = take(p->total * ts);
     const size_t o_f = take(p->total * ts);
     const size_t o_A = take(p->total_h * ts);
@@ -218,6 +201,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     const size_t o_cbase = take(sizeof(uint32_t) * cbase);
     const size_t o_tw = take(twb);
     const size_t o_cls = take(sizeof(int) * njobs);
+    const size_t o_lags = take(sizeof(uint32_t) * kMaxLags);
     const size_t o_tabc = take(sizeof(int) * 2 * p->ntab);  // all, then per class
     const size_t o_tab = take(sizeof(double) * (kErdfTable + 1) * p->ntab);
     const size_t o_rx = prec == LC_FP32 ? take(rxb) : 0;
@@ -235,6 +219,8 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->d_eff_iters = (uint32_t*)(base + o_eff);
     p->d_iter = (int*)(base + o_iter);
     p->d_partial = (double*)(base + o_partial);
+    p->d_lags = (uint32_t*)(base + o_lags);
+    p->partial_total = partial;
     p->d_x = base + o_x;
     p->d_f = base + o_f;
     p->d_A = base + o_A;
@@ -452,26 +438,10 @@ void plan_free(Plan* p)
     delete p;
 }
 
-struct StreamJoin {
-    Plan& p;
-    cudaStream_t user;
-    StreamJoin(Plan& pl, void* s) : p(pl), user((cudaStream_t)s)
-    {
-        cudaEventRecord(p.ev_in, user);
-        cudaStreamWaitEvent(p.stream, p.ev_in, 0);
-    }
-    ~StreamJoin()
-    {
-        cudaEventRecord(p.ev_out, p.stream);
-        cudaStreamWaitEvent(user, p.ev_out, 0);
-    }
-};
-
 }  // namespace lc
 
 using namespace lc;
 
-struct lc_plan_s : public lc::Plan {};
 
 extern "C" {
 

@@ -22,6 +22,8 @@ struct CurveDev {
     int32_t cls;
     uint64_t seed, curve_id;
     int32_t kind;                         // lc_erdf_kind
+    int32_t coeffs;                       // lc_tk_coeffs
+    int32_t targets;                      // lc_targets
     int32_t pad;
     double sigma;                         // log-normal width (dex)
     uint64_t tab;                         // tabulated shapes: offset of the CDF table (doubles)

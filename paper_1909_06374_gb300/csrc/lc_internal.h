@@ -52,7 +52,8 @@ struct Plan {
     CurveDev* d_curves = nullptr;
     ErdfConst* d_erdf = nullptr;
     double* d_sigma = nullptr;
-    double* d_partial = nullptr;
+    double* d_partial = nullptr;   // TK95 variance partials: realised, then (at partial_total) PSD
+    size_t partial_total = 0;
     uint32_t* d_eff_iters = nullptr;
     int* d_iter = nullptr;
     void* d_x = nullptr;       // state, sum N (T)
@@ -68,6 +69,7 @@ struct Plan {
     uint32_t* d_cbase = nullptr;
     size_t tw_bytes = 0;
     void* d_tk_stage = nullptr;  // lazily allocated for lc_generate_host
+    uint32_t* d_lags = nullptr;  // structure-function lags (kMaxLags)
     size_t ntab = 0;             // curves with a tabulated ERDF
     int* d_tab_curves = nullptr; // their indices (device)
     double* d_tab = nullptr;     // their CDF tables, kErdfTable + 1 doubles each
@@ -91,6 +93,9 @@ struct Plan {
 
 // ConvDev of a plan: null pointers when the convergence test is off.
 inline ConvDev conv_of(const Plan& p) { return p.conv_on ? p.conv : ConvDev{}; }
+
+// lags of one lc_structure_function call
+constexpr size_t kMaxLags = 4096;
 
 // setup stage (lc_setup.cu)
 int spec_blocks_per_curve(uint32_t log2n);
@@ -165,4 +170,48 @@ lc_status plan_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* launches)
 lc_status plan_continue(Plan& p, uint32_t n_it, cudaStream_t st, uint64_t* launches);
 void plan_free(Plan* p);
 
+// host helpers of the entry points
+#define LC_CK(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ::lc::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+            return LC_ERR_CUDA;                                                              \
+        }                                                                                    \
+    } while (0)
+
+// makes `dev` current for the scope of the guard
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// orders the plan's stream after the caller's stream on entry and the
+// caller's stream after the plan's on exit
+struct StreamJoin {
+    Plan& p;
+    cudaStream_t user;
+    StreamJoin(Plan& pl, void* s) : p(pl), user((cudaStream_t)s)
+    {
+        cudaEventRecord(p.ev_in, user);
+        cudaStreamWaitEvent(p.stream, p.ev_in, 0);
+    }
+    ~StreamJoin()
+    {
+        cudaEventRecord(p.ev_out, p.stream);
+        cudaStreamWaitEvent(user, p.ev_out, 0);
+    }
+};
+
 }  // namespace lc
+
+// the opaque handle of the C ABI
+struct lc_plan_s : public lc::Plan {};

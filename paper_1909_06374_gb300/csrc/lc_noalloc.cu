@@ -92,10 +92,11 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     auto take = [&](size_t bytes) { char* q = b + at; at = up256(at + bytes); return (void*)q; };
     p.d_curves = (CurveDev*)take(sizeof(CurveDev));
     p.d_erdf = (ErdfConst*)take(sizeof(ErdfConst));
-    p.d_sigma = (double*)take(sizeof(double));
+    p.d_sigma = (double*)take(sizeof(double) * 2);
     p.d_eff_iters = (uint32_t*)take(sizeof(uint32_t));
     p.d_iter = (int*)take(4 * sizeof(int));
-    p.d_partial = (double*)take(sizeof(double) * (size_t)spec_blocks_per_curve(k.log2n));
+    p.d_partial = (double*)take(sizeof(double) * 2 * (size_t)spec_blocks_per_curve(k.log2n));
+    p.partial_total = (size_t)spec_blocks_per_curve(k.log2n);
     p.d_x = take(n * ts);
     p.d_f = take(n * ts);
     p.d_A = take(nh * ts);

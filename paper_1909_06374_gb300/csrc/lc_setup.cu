@@ -14,17 +14,22 @@ constexpr int kSpecTile = kSpecBlock * kSpecPerThread;  // bins per block
 // real Nyquist bin sqrt(P_{N/2}) g_re; g from Box-Muller on the two uniforms
 // of Philox block j (stream 0).  Also the block's share of
 // sigma^2 = X_{N/2}^2 + 2 sum_{0<j<N/2} |X_j|^2 (Parseval for the
-// unnormalised inverse transform), reduced in a fixed order.
+// unnormalised inverse transform), reduced in a fixed order, and the same sum
+// with |X_j|^2 replaced by P_j (the variance the PSD implies, for PSD target
+// amplitudes).  coeffs = fixed amplitude: X_j = sqrt(P_j) e^{2 pi i U2},
+// X_{N/2} = +-sqrt(P_{N/2}) with the sign of cos(2 pi U2).
 __global__ void __launch_bounds__(kSpecBlock)
 k_tk_spectrum(const CurveDev* __restrict__ curves, const int* __restrict__ cls_curves,
-              int blocks_per_curve, double2* __restrict__ spec, double* __restrict__ partial)
+              int blocks_per_curve, double2* __restrict__ spec, double* __restrict__ partial,
+              double* __restrict__ partial_p)
 {
     const int ci = blockIdx.x / blocks_per_curve;
     const int jb = blockIdx.x % blocks_per_curve;
     const CurveDev cv = curves[cls_curves[ci]];
     const uint64_t nh = 1ull << (cv.log2n - 1);
     const double nd = (double)(1ull << cv.log2n);
-    double acc = 0.0;
+    const bool fixed = cv.coeffs == 1;
+    double acc = 0.0, acc_p = 0.0;
 #pragma unroll
     for (int q = 0; q < kSpecPerThread; ++q) {
         const uint64_t j = (uint64_t)jb * kSpecTile + (uint64_t)q * kSpecBlock + threadIdx.x;
@@ -33,49 +38,66 @@ k_tk_spectrum(const CurveDev* __restrict__ curves, const int* __restrict__ cls_c
         if (j > 0) {
             const uint4 w = philox(j, cv.curve_id, 0u, cv.seed);
             const double U1 = unit_open(w.x, w.y), U2 = unit_open(w.z, w.w);
-            const double rad = sqrt(-2.0 * log(U1));
+            const double rad = fixed ? 1.0 : sqrt(-2.0 * log(U1));
             double sn, cs;
             sincospi(2.0 * U2, &sn, &cs);
             const double f = (double)j / (nd * cv.dt);
             const double y = f / cv.f_br;
             const double P = 1.0 / (pow(y, cv.a_lo) + pow(y, cv.a_hi));
             if (j < nh) {
-                const double a = sqrt(P * 0.5);
+                const double a = fixed ? sqrt(P) : sqrt(P * 0.5);
                 X = make_double2(a * rad * cs, a * rad * sn);
                 acc += 2.0 * (X.x * X.x + X.y * X.y);
+                acc_p += 2.0 * P;
             } else {
-                X = make_double2(sqrt(P) * rad * cs, 0.0);
+                X = make_double2(fixed ? (cs < 0.0 ? -sqrt(P) : sqrt(P)) : sqrt(P) * rad * cs, 0.0);
                 acc += X.x * X.x;
+                acc_p += P;
             }
         }
         spec[cv.offh + j] = X;
     }
-    __shared__ double red[kSpecBlock];
+    __shared__ double red[kSpecBlock], red_p[kSpecBlock];
     red[threadIdx.x] = acc;
+    red_p[threadIdx.x] = acc_p;
     __syncthreads();
     for (int s = kSpecBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        if (threadIdx.x < s) {
+            red[threadIdx.x] += red[threadIdx.x + s];
+            red_p[threadIdx.x] += red_p[threadIdx.x + s];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = red[0];
+        partial_p[blockIdx.x] = red_p[0];
+    }
 }
 
-// sigma of each curve of a class: its partial sums added in block order.
+// sigma (realised) and sigma_P (PSD) of each curve of a class: the partial
+// sums added in block order.
 __global__ void k_sigma(const int* __restrict__ cls_curves, int ncurves, int blocks_per_curve,
-                        const double* __restrict__ partial, double* __restrict__ sigma)
+                        const double* __restrict__ partial, const double* __restrict__ partial_p,
+                        double* __restrict__ sigma, double* __restrict__ sigma_p)
 {
     const int ci = blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= ncurves) return;
-    double s = 0.0;
-    for (int b = 0; b < blocks_per_curve; ++b) s += partial[(size_t)ci * blocks_per_curve + b];
+    double s = 0.0, sp = 0.0;
+    for (int b = 0; b < blocks_per_curve; ++b) {
+        s += partial[(size_t)ci * blocks_per_curve + b];
+        sp += partial_p[(size_t)ci * blocks_per_curve + b];
+    }
     sigma[cls_curves[ci]] = sqrt(s);
+    sigma_p[cls_curves[ci]] = sqrt(sp);
 }
 
-// Target amplitudes of the normalised TK95 series: A_j = |X_j| / sigma, A_0 = 0.
+// Target amplitudes of the normalised TK95 series: A_j = |X_j| / sigma, A_0 = 0;
+// with PSD targets A_j = sqrt(P_j) / sigma_P.
 template <typename T>
 __global__ void k_amplitudes(const CurveDev* __restrict__ curves, const int* __restrict__ cls_curves,
                              int ncurves, uint32_t log2n, const double2* __restrict__ spec,
-                             const double* __restrict__ sigma, T* __restrict__ A)
+                             const double* __restrict__ sigma, const double* __restrict__ sigma_p,
+                             T* __restrict__ A)
 {
     const uint64_t nh1 = (1ull << (log2n - 1)) + 1;
     const uint64_t total = (uint64_t)ncurves * nh1;
@@ -84,9 +106,16 @@ __global__ void k_amplitudes(const CurveDev* __restrict__ curves, const int* __r
         const int ci = (int)(t / nh1);
         const uint64_t j = t - (uint64_t)ci * nh1;
         const int c = cls_curves[ci];
-        const uint64_t offh = curves[c].offh;
-        const double2 X = spec[offh + j];
-        const double a = j == 0 ? 0.0 : hypot(X.x, X.y) / sigma[c];
+        const CurveDev& cv = curves[c];
+        const uint64_t offh = cv.offh;
+        double a = 0.0;
+        if (j > 0 && cv.targets == 1) {
+            const double y = (double)j / ((double)(1ull << log2n) * cv.dt) / cv.f_br;
+            a = sqrt(1.0 / (pow(y, cv.a_lo) + pow(y, cv.a_hi))) / sigma_p[c];
+        } else if (j > 0) {
+            const double2 X = spec[offh + j];
+            a = hypot(X.x, X.y) / sigma[c];
+        }
         A[offh + j] = (T)a;
     }
 }
@@ -188,10 +217,11 @@ int spec_blocks_per_curve(uint32_t log2n)
 void launch_tk_spectrum(const Plan& p, const ClassInfo& k, cudaStream_t st)
 {
     const int bpc = spec_blocks_per_curve(k.log2n);
-    k_tk_spectrum<<<k.ncurves * bpc, kSpecBlock, 0, st>>>(p.d_curves, k.d_curves, bpc, p.d_spec,
-                                                         p.d_partial + k.partial_off);
-    k_sigma<<<(k.ncurves + 127) / 128, 128, 0, st>>>(k.d_curves, k.ncurves, bpc,
-                                                     p.d_partial + k.partial_off, p.d_sigma);
+    double* part = p.d_partial + k.partial_off;
+    double* part_p = p.d_partial + p.partial_total + k.partial_off;
+    k_tk_spectrum<<<k.ncurves * bpc, kSpecBlock, 0, st>>>(p.d_curves, k.d_curves, bpc, p.d_spec, part, part_p);
+    k_sigma<<<(k.ncurves + 127) / 128, 128, 0, st>>>(k.d_curves, k.ncurves, bpc, part, part_p, p.d_sigma,
+                                                     p.d_sigma + p.ncurves);
 }
 
 template <typename T>
@@ -199,7 +229,7 @@ void launch_amplitudes(const Plan& p, const ClassInfo& k, cudaStream_t st)
 {
     const uint64_t work = (uint64_t)k.ncurves * ((1ull << (k.log2n - 1)) + 1);
     k_amplitudes<T><<<grid_for(work, 256), 256, 0, st>>>(p.d_curves, k.d_curves, k.ncurves, k.log2n,
-                                                         p.d_spec, p.d_sigma, (T*)p.d_A);
+                                                         p.d_spec, p.d_sigma, p.d_sigma + p.ncurves, (T*)p.d_A);
 }
 
 void launch_erdf_constants(const Plan& p, cudaStream_t st)

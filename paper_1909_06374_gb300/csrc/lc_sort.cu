@@ -176,28 +176,38 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
     const uint32_t lt = (1u << lane) - 1u;
     K key[kSlots];
     uint32_t val[kSlots], rk[kSlots];
+    // ranking in two phases: every slot's load and peer mask first (independent
+    // chains that overlap), then the short chain of per-warp digit counters;
+    // every third slot takes its mask from the match pipe, the others from
+    // eight ballots on the ALU pipe
+    uint32_t info[kSlots];  // digit | below << 8 | count << 16; 0xffffffff: empty slot
 #pragma unroll
     for (int e = 0; e < kSlots; ++e) {
         const int j = e * 32 + lane;              // index within the warp's elements
         const int el = warp * EW + j;             // index within the tile
         const bool valid = j < EW && el < tl;
         K k = 0;
-        uint32_t v = 0, d = 0;
+        uint32_t v = 0, d = 256u + lane;          // empty slots never match a digit
         if (valid) {
             k = load_key<T, FIRST>(a, off + e0 + el);
             v = FIRST ? e0 + el : a.vals_in[off + e0 + el];
             d = (uint32_t)(k >> a.shift) & 255u;
         }
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
-        const uint32_t peers = peers8(d) & vm;
-        const uint32_t below = __popc(peers & lt);
+        const uint32_t peers = (e % 3 == 2 ? __match_any_sync(0xffffffffu, d) : peers8(d)) & vm;
+        key[e] = k;
+        val[e] = v;
+        info[e] = valid ? d | ((uint32_t)__popc(peers & lt) << 8) | ((uint32_t)__popc(peers) << 16) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int e = 0; e < kSlots; ++e) {
+        const bool valid = info[e] != 0xffffffffu;
+        const uint32_t d = info[e] & 255u, below = (info[e] >> 8) & 255u;
         uint32_t base = 0;
         if (valid) base = wcnt[warp][d];
         __syncwarp();
-        if (valid && below == 0) wcnt[warp][d] = base + __popc(peers);
+        if (valid && below == 0) wcnt[warp][d] = base + (info[e] >> 16);
         __syncwarp();
-        key[e] = k;
-        val[e] = v;
         rk[e] = valid ? base + below : 0xffffffffu;
     }
     __syncthreads();

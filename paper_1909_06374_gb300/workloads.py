@@ -33,7 +33,7 @@ import numpy as np
 
 BASE = dict(dt=1.0, f_br=1.0 / 300.0, alpha_low=1.0, alpha_high=2.0,
             log_lmin=-4.0, log_lmax=0.0, log_lbreak=-1.5, slope_low=0.4, slope_high=-2.5,
-            linear_space=0, erdf_kind=0, sigma=0.0)
+            linear_space=0, erdf_kind=0, sigma=0.0, tk_coeffs=0, tk_targets=0)
 
 ERDF_SHAPES = {
     "smooth_eq1": dict(erdf_kind=1, log_lmin=-4.0, log_lmax=1.0, log_lbreak=-1.84,

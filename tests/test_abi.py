@@ -78,7 +78,7 @@ def test_status_strings():
                                  dict(slope_low=float("inf")), dict(erdf_kind=3), dict(erdf_kind=-1),
                                  dict(erdf_kind=2, sigma=0.0), dict(erdf_kind=2, sigma=0.001),
                                  dict(erdf_kind=2, sigma=0.5, log_lbreak=-40.0),
-                                 dict(erdf_kind=1, log_lbreak=0.5)])
+                                 dict(erdf_kind=1, log_lbreak=0.5), dict(tk_coeffs=2), dict(tk_targets=-1)])
 def test_invalid_jobs_are_rejected_before_any_device_work(bad):
     j = workloads.job(10, 3, 0, 0)
     j.update(bad)

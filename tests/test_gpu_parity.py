@@ -47,6 +47,15 @@ JOBSETS = {
         workloads.job(17, 2, seed=25, curve_id=4, linear_space=1, **workloads.ERDF_SHAPES["lognormal"]),
         workloads.job(10, 3, seed=26, curve_id=5, linear_space=1, **workloads.ERDF_SHAPES["table2"]),
     ],
+    # PSD variants: fixed-amplitude TK coefficients, PSD target amplitudes, a
+    # single power law (equal slopes), on both iteration paths
+    "psd_variants": lambda: [
+        workloads.job(12, 3, seed=31, curve_id=0, tk_coeffs=1),
+        workloads.job(12, 3, seed=32, curve_id=1, tk_targets=1),
+        workloads.job(11, 3, seed=33, curve_id=2, tk_coeffs=1, tk_targets=1, alpha_low=1.5, alpha_high=1.5),
+        workloads.job(17, 2, seed=34, curve_id=3, tk_coeffs=1, tk_targets=1),
+        workloads.job(8, 3, seed=35, curve_id=4, alpha_low=2.2, alpha_high=2.2),
+    ],
 }
 
 
