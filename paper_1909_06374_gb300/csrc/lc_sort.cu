@@ -146,33 +146,22 @@ constexpr int kSlots = kSortTile / kSortThreads;  // elements per thread of a fu
 // (warp w owns elements [w T/8, (w+1) T/8), lane-striped; ballot multisplit
 // within the warp, per-warp digit counts, one block scan), placed in a
 // digit-sorted shared copy, and written out run by run, so that consecutive
-// threads write consecutive addresses of a digit's output range.
+// threads write consecutive addresses of a digit's output range; digit d's
+// run starts at gb[d] within the curve.
 // MODE 0: sorted (key, position) pairs; kSortArgsortScatter: x[position] =
 // s[rank]; kSortKeysToValues: s[rank] = value.
+// Expects wcnt zeroed and gb set (after a block barrier); returns the tile's
+// count of digit threadIdx.x.  Ends with a block barrier.
 template <typename T, bool FIRST, int MODE>
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
+__device__ __forceinline__ uint32_t sort_tile(const SortArgs& a, const void* kin, const uint32_t* vin, void* kout,
+                                              uint32_t* vout, int shift, uint64_t off, uint32_t e0, int tl,
+                                              typename key_of<T>::type* sk, uint32_t* sv,
+                                              uint32_t (*wcnt)[256], uint32_t* ldstart, const uint32_t* gb,
+                                              uint32_t* wsum)
 {
     using K = typename key_of<T>::type;
-    const int ci = blockIdx.x / a.tpc;
-    const int t = blockIdx.x % a.tpc;
-    const int c = a.cls_curves[ci];
-    if (!curve_active(a, c)) return;
-    __shared__ K sk[kSortTile];
-    __shared__ uint32_t sv[kSortTile];
-    __shared__ uint32_t wcnt[kSortWarps][256];
-    __shared__ uint32_t ldstart[256];
-    __shared__ uint32_t gb[256];
-    __shared__ uint32_t wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tl = a.tile_len;
     const int EW = (tl + kSortWarps - 1) / kSortWarps;  // elements per warp
-#pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) wcnt[w][tid] = 0;
-    gb[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
-              a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
-    __syncthreads();
-    const uint64_t off = a.curves[c].off;
-    const uint32_t e0 = (uint32_t)t * (uint32_t)tl;
     const uint32_t lt = (1u << lane) - 1u;
     K key[kSlots];
     uint32_t val[kSlots], rk[kSlots];
@@ -189,9 +178,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
         K k = 0;
         uint32_t v = 0, d = 256u + lane;          // empty slots never match a digit
         if (valid) {
-            k = load_key<T, FIRST>(a, off + e0 + el);
-            v = FIRST ? e0 + el : a.vals_in[off + e0 + el];
-            d = (uint32_t)(k >> a.shift) & 255u;
+            k = FIRST ? order_key(((const T*)a.src)[off + e0 + el]) : ((const K*)kin)[off + e0 + el];
+            v = FIRST ? e0 + el : vin[off + e0 + el];
+            d = (uint32_t)(k >> shift) & 255u;
         }
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
         const uint32_t peers = (e % 3 == 2 ? __match_any_sync(0xffffffffu, d) : peers8(d)) & vm;
@@ -234,7 +223,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
 #pragma unroll
     for (int e = 0; e < kSlots; ++e) {
         if (rk[e] != 0xffffffffu) {
-            const uint32_t d = (uint32_t)(key[e] >> a.shift) & 255u;
+            const uint32_t d = (uint32_t)(key[e] >> shift) & 255u;
             const uint32_t lp = ldstart[d] + wcnt[warp][d] + rk[e];
             sk[lp] = key[e];
             sv[lp] = val[e];
@@ -251,7 +240,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
             const int i = tid + e * kSortThreads;
             if (i < tl) {
                 const K k = sk[i];
-                const uint32_t d = (uint32_t)(k >> a.shift) & 255u;
+                const uint32_t d = (uint32_t)(k >> shift) & 255u;
                 const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
                 pos[e] = sv[i];
                 xn[e] = ((const T*)a.s_in)[off + dest];
@@ -263,16 +252,44 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const SortArgs a)
     } else {
         for (int i = tid; i < tl; i += kSortThreads) {
             const K k = sk[i];
-            const uint32_t d = (uint32_t)(k >> a.shift) & 255u;
+            const uint32_t d = (uint32_t)(k >> shift) & 255u;
             const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
             if (MODE == 0) {
-                ((K*)a.keys_out)[off + dest] = k;
-                a.vals_out[off + dest] = sv[i];
+                ((K*)kout)[off + dest] = k;
+                vout[off + dest] = sv[i];
             } else {
                 ((T*)a.s_out)[off + dest] = key_value(k);
             }
         }
     }
+    __syncthreads();
+    return tot;
+}
+
+// One pass over one tile per block: the tile's output bases come from the
+// per-tile histograms and their two-level scan.
+template <typename T, bool FIRST, int MODE>
+__global__ void __launch_bounds__(kSortThreads, 5) k_sort_scatter(const SortArgs a)
+{
+    using K = typename key_of<T>::type;
+    const int ci = blockIdx.x / a.tpc;
+    const int t = blockIdx.x % a.tpc;
+    const int c = a.cls_curves[ci];
+    if (!curve_active(a, c)) return;
+    __shared__ K sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ uint32_t wcnt[kSortWarps][256];
+    __shared__ uint32_t ldstart[256];
+    __shared__ uint32_t gb[256];
+    __shared__ uint32_t wsum[8];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][tid] = 0;
+    gb[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
+              a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
+    __syncthreads();
+    sort_tile<T, FIRST, MODE>(a, a.keys_in, a.vals_in, a.keys_out, a.vals_out, a.shift, a.curves[c].off,
+                              (uint32_t)t * (uint32_t)a.tile_len, a.tile_len, sk, sv, wcnt, ldstart, gb, wsum);
 }
 
 // Eq. 4 (Sec. 3.2.2) from the two iterates, both in natural order: one tile
