@@ -331,12 +331,18 @@ static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches)
         // with the convergence test the FFTs work in d_f and d_keysB (free
         // until the sort starts) so that x_{i-1} stays in d_x for Eq. 4
         void* alt = p.conv_on ? p.d_keysB : p.d_x;
-        void* R1 = launch_fft<T>(p, k, false, p.d_x, p.d_f, nullptr, true, st, launches,
-                                 p.conv_on ? p.d_keysB : nullptr);
-        void* Zp = (R1 == p.d_f) ? alt : p.d_f;
-        launch_spectral_iter<T>(p, k, R1, Zp, st);
-        ++*launches;
-        void* R3 = launch_fft<T>(p, k, true, Zp, R1, nullptr, true, st, launches);
+        void* R3;
+        if (k.log2n - 1 >= 12) {
+            // tile path: the spectral step runs inside the transforms' middle passes
+            R3 = launch_fft_iteration<T>(p, k, p.d_x, p.d_f, alt, st, launches);
+        } else {
+            void* R1 = launch_fft<T>(p, k, false, p.d_x, p.d_f, nullptr, true, st, launches,
+                                     p.conv_on ? p.d_keysB : nullptr);
+            void* Zp = (R1 == p.d_f) ? alt : p.d_f;
+            launch_spectral_iter<T>(p, k, R1, Zp, st);
+            ++*launches;
+            R3 = launch_fft<T>(p, k, true, Zp, R1, nullptr, true, st, launches);
+        }
         if (!p.conv_on) {
             launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches);
         } else {

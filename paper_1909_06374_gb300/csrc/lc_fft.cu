@@ -23,6 +23,51 @@ __device__ __forceinline__ cplx<T> twiddle_M(const cplx<T>* __restrict__ rt, uin
     return w;
 }
 
+// W_M^e (e < M <= 2^26) from three shared-memory tables of 512 entries,
+// W^e = W^{e2 2^18} W^{e1 2^9} W^{e0} (e = e2 2^18 + e1 2^9 + e0; the top
+// level only when M > 2^18), each entry read from the class table once per
+// block.  Replaces scattered reads of the class table, whose per-block
+// footprint is several times the block's data.
+constexpr int kTwLevel = 512;
+template <typename T>
+struct SmemTw {
+    const cplx<T>* t0;
+    const cplx<T>* t1;
+    const cplx<T>* t2;
+    bool three;
+    __device__ __forceinline__ cplx<T> operator()(uint64_t e) const
+    {
+        cplx<T> w = cmul(t1[(e >> 9) & (kTwLevel - 1)], t0[e & (kTwLevel - 1)]);
+        if (three) w = cmul(t2[e >> 18], w);
+        return w;
+    }
+};
+
+// Fills the tables at `mem` (3 x 512 entries) for a length-M transform;
+// ends with a block barrier.
+template <typename T>
+__device__ __forceinline__ SmemTw<T> build_smem_tw(cplx<T>* mem, const cplx<T>* __restrict__ rt, int log2M)
+{
+    const uint64_t M = 1ull << log2M;
+    SmemTw<T> tw;
+    tw.t0 = mem;
+    tw.t1 = mem + kTwLevel;
+    tw.t2 = mem + 2 * kTwLevel;
+    tw.three = log2M > 18;
+    const int n1 = log2M >= 18 ? kTwLevel : (1 << (log2M - 9));
+    const int n2 = log2M > 18 ? (1 << (log2M - 18)) : 0;
+    for (int x = threadIdx.x; x < kTwLevel + n1 + n2; x += blockDim.x) {
+        uint64_t e;
+        if (x < kTwLevel) e = (uint64_t)x;
+        else if (x < kTwLevel + n1) e = (uint64_t)(x - kTwLevel) << 9;
+        else e = (uint64_t)(x - kTwLevel - n1) << 18;
+        const int slot = x < kTwLevel + n1 ? x : 2 * kTwLevel + (x - kTwLevel - n1);
+        mem[slot] = twiddle_M<T>(rt, e, M);
+    }
+    __syncthreads();
+    return tw;
+}
+
 // Table e^{-2 pi i k/N}, k < N/2, computed in FP64 and rounded once to T.
 template <typename T>
 __global__ void k_twiddles(cplx<T>* __restrict__ rt, uint32_t log2n)
@@ -106,7 +151,7 @@ constexpr int kTileStride = kTileCols + 1;
 
 template <typename T, int Q, bool INV>
 __device__ __forceinline__ void tile_subpass(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int LR,
-                                             int log2p2, const cplx<T>* __restrict__ rt, uint64_t M, int log2M)
+                                             int log2p2, const SmemTw<T>& tw, int log2M)
 {
     using V = cplx<T>;
     constexpr int LQ = ilog2c(Q);
@@ -125,7 +170,7 @@ __device__ __forceinline__ void tile_subpass(const cplx<T>* __restrict__ in, cpl
             const uint64_t step = (uint64_t)k2 << (log2M - LQ - log2p2);
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                V w = twiddle_M<T>(rt, (uint64_t)q * step, M);
+                V w = tw((uint64_t)q * step);
                 if (INV) w.y = -w.y;
                 u[q] = cmul(u[q], w);
             }
@@ -145,6 +190,7 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
     extern __shared__ __align__(16) unsigned char tile_smem[];
     V* b0 = (V*)tile_smem;
     V* b1 = b0 + R * kTileStride;
+    V* twm = b1 + R * kTileStride;
     const uint32_t log2nb = a.log2M - LR;
     const int tpc = 1 << (log2nb - 4);       // tiles per curve (nb >= 16)
     const int ci = blockIdx.x / tpc;
@@ -157,7 +203,6 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
     const V* __restrict__ rt = (const V*)a.tw;
     const uint64_t nb = 1ull << log2nb;
     const uint64_t p = 1ull << a.log2p;
-    const uint64_t M = 1ull << a.log2M;
     const uint64_t i0 = (uint64_t)ti * kTileCols;
     constexpr int PER = R * kTileCols / 256;  // elements per thread
     V v[PER];
@@ -166,6 +211,7 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
         const int idx = threadIdx.x + e * 256;
         v[e] = src[i0 + (idx & (kTileCols - 1)) + (uint64_t)(idx >> 4) * nb];
     }
+    const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M);
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
         const int idx = threadIdx.x + e * 256;
@@ -173,7 +219,7 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
         V x = v[e];
         if (p > 1) {
             const uint64_t k = (i0 + j) & (p - 1);
-            V w = twiddle_M<T>(rt, ((uint64_t)r * k) << (a.log2M - LR - a.log2p), M);
+            V w = tw(((uint64_t)r * k) << (a.log2M - LR - a.log2p));
             if (INV) w.y = -w.y;
             x = cmul(x, w);
         }
@@ -185,13 +231,13 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
     int log2p2 = 0;
     constexpr int rem = LR & 3;
     if (rem) {
-        tile_subpass<T, (1 << (rem ? rem : 1)), INV>(in, out, LR, 0, rt, M, a.log2M);
+        tile_subpass<T, (1 << (rem ? rem : 1)), INV>(in, out, LR, 0, tw, a.log2M);
         __syncthreads();
         log2p2 = rem;
         V* t = in; in = out; out = t;
     }
     for (; log2p2 < LR; log2p2 += 4) {
-        tile_subpass<T, 16, INV>(in, out, LR, log2p2, rt, M, a.log2M);
+        tile_subpass<T, 16, INV>(in, out, LR, log2p2, tw, a.log2M);
         __syncthreads();
         V* t = in; in = out; out = t;
     }
@@ -342,6 +388,147 @@ __global__ void __launch_bounds__(256) k_spectral_tk(const SpecArgs a)
     }
 }
 
+// One conjugate pair (t, M - t) of the spectral step on values held by the
+// caller: za = Z_t, zb = Z_{M-t} in, Z'_t, Z'_{M-t} out.  The arithmetic runs
+// on the representative k = min(t, M - t), as in k_spectral_iter.
+template <typename T>
+__device__ __forceinline__ void spectral_pair_tk(cplx<T>& za, cplx<T>& zb, uint64_t t, uint64_t M,
+                                                 const cplx<T>* __restrict__ rt, const T* __restrict__ A)
+{
+    using V = cplx<T>;
+    const bool low = 2 * t < M;
+    const uint64_t k = low ? t : M - t;
+    const V zk = low ? za : zb, zm = low ? zb : za;
+    const V W = rt[k];
+    V E; E.x = (T)0.5 * (zk.x + zm.x); E.y = (T)0.5 * (zk.y - zm.y);
+    V O; O.x = (T)0.5 * (zk.y + zm.y); O.y = (T)-0.5 * (zk.x - zm.x);
+    const V WO = cmul(W, O);
+    const V Yk = keep_phase(cadd(E, WO), A[k]);
+    const V Ym = keep_phase(cconj(csub(E, WO)), A[M - k]);
+    V Zk, Zm;
+    pack_pair(Yk, Ym, W, Zk, Zm);
+    za = low ? Zk : Zm;
+    zb = low ? Zm : Zk;
+}
+
+// The middle of one iteration on the tile path, in one kernel: the forward
+// transform's last pass (radix R = 2^LR, span p = M/R), the spectral step, and
+// the inverse transform's first pass (radix R, span 1; the inverse runs its
+// passes in the reverse radix order).  Both passes touch column i through the
+// elements i + q p (q < R), and the conjugate partner M - t of t = i + q p is
+// in column p - i at row R-1-q; in column 0 itself at row R-q; and, for
+// i = p/2, in the same column at row R-1-q.  A block takes 8 columns and
+// their 8 partner columns -- column pairs (0, p/2), then (g, p - g) -- so all
+// three steps stay in shared memory, saving two passes over the spectrum and
+// the spectral kernel.  Output: y[i R + q] for the block's columns i.
+template <typename T, int LR>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft_spectral(const PassArgs a, const void* __restrict__ A_all)
+{
+    using V = cplx<T>;
+    constexpr int R = 1 << LR;
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    V* b0 = (V*)tile_smem;
+    V* b1 = b0 + R * kTileStride;
+    V* twm = b1 + R * kTileStride;
+    const uint32_t log2p = a.log2M - LR;
+    const uint64_t p = 1ull << log2p;
+    const int tpc = (int)(p >> 4);
+    const int ci = blockIdx.x / tpc;
+    const int ti = blockIdx.x % tpc;
+    const int c = a.cls_curves[ci];
+    if (a.d_iter && (uint32_t)(*a.d_iter) >= a.eff_iters[c]) return;
+    const CurveDev& cv = a.curves[c];
+    const uint64_t base = cv.off >> 1;
+    const V* __restrict__ src = (const V*)a.in + base;
+    V* __restrict__ dst = (V*)a.out + base;
+    const T* __restrict__ A = (const T*)A_all + cv.offh;
+    const V* __restrict__ rt = (const V*)a.tw;
+    const uint64_t M = 1ull << a.log2M;
+    // slot j < 8: column g = 8 ti + j; slot j + 8: its partner (p/2 for g = 0)
+    auto column = [&](int j) -> uint64_t {
+        const uint64_t g = (uint64_t)ti * 8 + (uint64_t)(j & 7);
+        if (j < 8) return g;
+        return g == 0 ? p / 2 : p - g;
+    };
+    constexpr int PER = R * kTileCols / 256;  // elements per thread
+    V v[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {  // every load in flight before any use
+        const int idx = threadIdx.x + e * 256;
+        v[e] = src[column(idx & (kTileCols - 1)) + (uint64_t)(idx >> 4) * p];
+    }
+    const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M);
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        const int idx = threadIdx.x + e * 256;
+        const int r = idx >> 4, j = idx & (kTileCols - 1);
+        // forward last pass: W_{R p}^{r k} = W_M^{r i} (k = i < p)
+        b0[r * kTileStride + j] = cmul(v[e], tw((uint64_t)r * column(j)));
+    }
+    __syncthreads();
+    V* in = b0;
+    V* out = b1;
+    int log2p2 = 0;
+    constexpr int rem = LR & 3;
+    if (rem) {
+        tile_subpass<T, (1 << (rem ? rem : 1)), false>(in, out, LR, 0, tw, a.log2M);
+        __syncthreads();
+        log2p2 = rem;
+        V* t = in; in = out; out = t;
+    }
+    for (; log2p2 < LR; log2p2 += 4) {
+        tile_subpass<T, 16, false>(in, out, LR, log2p2, tw, a.log2M);
+        __syncthreads();
+        V* t = in; in = out; out = t;
+    }
+    // spectral step on the conjugate pairs, in place: in[q][j] = Z_{column(j) + q p}
+    for (int idx = threadIdx.x; idx < R * 8; idx += 256) {
+        const int q = idx >> 3, j = idx & 7;
+        const uint64_t col = column(j);
+        const uint64_t t = col + (uint64_t)q * p;
+        if (col == 0) {
+            if (q == 0) {  // DC and Nyquist: Y_0 = A_0, Y_M = A_M sign(X_M), packed together
+                const V z0 = in[0];
+                const T XM = z0.x - z0.y;
+                const T Y0 = A[0];
+                const T YM = XM < (T)0 ? -A[M] : A[M];
+                V o; o.x = Y0 + YM; o.y = Y0 - YM;
+                in[0] = o;
+            } else if (q == R / 2) {  // k = M/2 pairs with itself: X = conj(Z), packed 2 conj(Y)
+                const V Yh = keep_phase(cconj(in[q * kTileStride]), A[M >> 1]);
+                V oh; oh.x = (T)2 * Yh.x; oh.y = -(T)2 * Yh.y;
+                in[q * kTileStride] = oh;
+            } else if (q < R / 2) {
+                spectral_pair_tk<T>(in[q * kTileStride], in[(R - q) * kTileStride], t, M, rt, A);
+            }
+        } else {
+            spectral_pair_tk<T>(in[q * kTileStride + j], in[(R - 1 - q) * kTileStride + j + 8], t, M, rt, A);
+        }
+        if (ti == 0 && j == 0 && q < R / 2) {  // column p/2 pairs with itself
+            spectral_pair_tk<T>(in[q * kTileStride + 8], in[(R - 1 - q) * kTileStride + 8], p / 2 + (uint64_t)q * p,
+                                M, rt, A);
+        }
+    }
+    __syncthreads();
+    // inverse first pass (span 1: no input twiddle)
+    log2p2 = 0;
+    if (rem) {
+        tile_subpass<T, (1 << (rem ? rem : 1)), true>(in, out, LR, 0, tw, a.log2M);
+        __syncthreads();
+        log2p2 = rem;
+        V* t = in; in = out; out = t;
+    }
+    for (; log2p2 < LR; log2p2 += 4) {
+        tile_subpass<T, 16, true>(in, out, LR, log2p2, tw, a.log2M);
+        __syncthreads();
+        V* t = in; in = out; out = t;
+    }
+    for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
+        const int j = idx >> LR, q = idx & (R - 1);
+        dst[(column(j) << LR) + q] = in[q * kTileStride + j];
+    }
+}
+
 // ------------------------------------------------------------ launchers
 static int grid_for(uint64_t work, int block)
 {
@@ -396,7 +583,7 @@ std::vector<int> tile_radices(uint32_t log2m, bool fp64)
 template <typename T, int LR, bool INV>
 static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
 {
-    const size_t smem = (size_t)2 * ((size_t)1 << LR) * kTileStride * sizeof(cplx<T>);
+    const size_t smem = ((size_t)2 * ((size_t)1 << LR) * kTileStride + 3 * kTwLevel) * sizeof(cplx<T>);
     cudaFuncSetAttribute(k_fft_tile<T, LR, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fft_tile<T, LR, INV><<<blocks, 256, smem, st>>>(a);
 }
@@ -497,12 +684,85 @@ void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_
     k_spectral_tk<T><<<grid_for(work, 256), 256, 0, st>>>(a);
 }
 
+// Forward transform, spectral step and inverse transform of one iteration
+// on the tile path (log2 M >= 12): the forward passes but the last, the fused
+// k_fft_spectral, then the inverse passes in reverse radix order.  Buffers:
+// `in` is read by the first pass only; the passes alternate between b and c
+// (c may be `in` itself).  Returns the buffer with x_adj.
+template <typename T>
+void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b, void* c, cudaStream_t st,
+                           uint64_t* launches)
+{
+    PassArgs a;
+    a.cls_curves = k.d_curves;
+    a.curves = p.d_curves;
+    a.eff_iters = p.d_eff_iters;
+    a.d_iter = p.d_iter;
+    a.tw = k.d_tw;
+    a.ncurves = k.ncurves;
+    a.log2M = k.log2n - 1;
+    const std::vector<int> lr = tile_radices(a.log2M, sizeof(T) == 8);
+    const int P = (int)lr.size();
+    void* cur = in;
+    void* nxt = b;
+    auto step = [&]() { void* w = nxt; nxt = (w == b) ? c : b; cur = w; };
+    uint32_t log2p = 0;
+    for (int q = 0; q + 1 < P; ++q) {
+        a.in = cur; a.out = nxt; a.log2p = log2p;
+        launch_tile<T, false>(lr[q], a, k.ncurves << (a.log2M - lr[q] - 4), st);
+        if (launches) ++*launches;
+        log2p += (uint32_t)lr[q];
+        step();
+    }
+    const int LR = lr[P - 1];
+    a.in = cur; a.out = nxt; a.log2p = log2p;
+    {
+        const int blocks = k.ncurves << (a.log2M - LR - 4);
+        const size_t smem = ((size_t)2 * ((size_t)1 << LR) * kTileStride + 3 * kTwLevel) * sizeof(cplx<T>);
+        switch (LR) {
+#define LC_FUSED_CASE(L)                                                                                   \
+    case L:                                                                                                \
+        cudaFuncSetAttribute(k_fft_spectral<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_fft_spectral<T, L><<<blocks, 256, smem, st>>>(a, p.d_A);                                          \
+        break;
+            LC_FUSED_CASE(5)
+            LC_FUSED_CASE(6)
+            LC_FUSED_CASE(7)
+            LC_FUSED_CASE(8)
+#undef LC_FUSED_CASE
+        default:
+            if (sizeof(T) == 4 && LR == 9) {
+                cudaFuncSetAttribute(k_fft_spectral<float, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_fft_spectral<float, 9><<<blocks, 256, smem, st>>>(a, p.d_A);
+            } else {
+                set_error("internal: unsupported fused radix");
+            }
+            break;
+        }
+        if (launches) ++*launches;
+    }
+    step();
+    log2p = (uint32_t)LR;
+    for (int q = P - 2; q >= 0; --q) {
+        a.in = cur; a.out = nxt; a.log2p = log2p;
+        launch_tile<T, true>(lr[q], a, k.ncurves << (a.log2M - lr[q] - 4), st);
+        if (launches) ++*launches;
+        log2p += (uint32_t)lr[q];
+        step();
+    }
+    return cur;
+}
+
 template void launch_twiddles<float>(const ClassInfo&, cudaStream_t);
 template void launch_twiddles<double>(const ClassInfo&, cudaStream_t);
 template void* launch_fft<float>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*,
                                  void*);
 template void* launch_fft<double>(const Plan&, const ClassInfo&, bool, void*, void*, void*, bool, cudaStream_t, uint64_t*,
                                   void*);
+template void* launch_fft_iteration<float>(const Plan&, const ClassInfo&, void*, void*, void*, cudaStream_t,
+                                           uint64_t*);
+template void* launch_fft_iteration<double>(const Plan&, const ClassInfo&, void*, void*, void*, cudaStream_t,
+                                            uint64_t*);
 template void launch_spectral_iter<float>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
 template void launch_spectral_iter<double>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
 template void launch_spectral_tk<float>(const Plan&, const ClassInfo&, void*, cudaStream_t);

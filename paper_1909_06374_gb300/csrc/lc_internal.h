@@ -120,6 +120,12 @@ template <typename T> void* launch_fft(const Plan& p, const ClassInfo& k, bool i
                                        uint64_t* launches, void* scratch = nullptr);
 template <typename T> void launch_spectral_iter(const Plan& p, const ClassInfo& k, const void* Z,
                                                 void* Zp, cudaStream_t st);
+// Forward FFT, spectral step and inverse FFT of one iteration of a tile-path
+// class (log2 N >= 13) with the spectral step fused between the two
+// transforms' middle passes; `in` is only read, the passes alternate between
+// b and c (c may be in); returns the buffer holding x_adj.  Gated.
+template <typename T> void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b, void* c,
+                                                 cudaStream_t st, uint64_t* launches);
 template <typename T> void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_t st);
 
 // sort stage (lc_sort.cu)

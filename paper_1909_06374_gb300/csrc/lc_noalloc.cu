@@ -145,10 +145,15 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
             launch_resident(p, k, job->iters, s, nullptr);
         } else {
             for (uint32_t it = 0; it < job->iters; ++it) {
-                void* R1 = launch_fft<float>(p, k, false, p.d_x, p.d_f, nullptr, true, s, nullptr);
-                void* Zp = (R1 == p.d_x) ? p.d_f : p.d_x;
-                launch_spectral_iter<float>(p, k, R1, Zp, s);
-                void* R3 = launch_fft<float>(p, k, true, Zp, R1, nullptr, true, s, nullptr);
+                void* R3;
+                if (k.log2n - 1 >= 12) {
+                    R3 = launch_fft_iteration<float>(p, k, p.d_x, p.d_f, p.d_x, s, nullptr);
+                } else {
+                    void* R1 = launch_fft<float>(p, k, false, p.d_x, p.d_f, nullptr, true, s, nullptr);
+                    void* Zp = (R1 == p.d_x) ? p.d_f : p.d_x;
+                    launch_spectral_iter<float>(p, k, R1, Zp, s);
+                    R3 = launch_fft<float>(p, k, true, Zp, R1, nullptr, true, s, nullptr);
+                }
                 launch_sort<float>(p, k, R3, kSortArgsortScatter, true, s, nullptr);
                 launch_iter_increment(p, s);
             }
