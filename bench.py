@@ -34,8 +34,16 @@ NCURVES, LOG2N, ITERS = 4096, 16, 200
 METRIC = "light-curve samples x E13 iterations per second"
 UNIT = "sample*iter/s"
 ALG_BYTES_PER_SAMPLE_ITER = 14  # read x 4 + read A 2 + read s 4 + write x 4 (FP32)
+# Algorithmic bytes of one argsort (all radix passes) per element, FP32 keys:
+# pass 0 reads the value and writes key + position (12 B), passes 1-2 read and
+# write key + position (16 B each), the last reads key + position and the
+# sorted draw and writes the state (16 B).  FP64: 8 passes of 8-byte keys.
+SORT_BYTES_PER_ELEMENT = {4: 12 + 16 + 16 + 16, 8: 20 + 6 * 24 + 28}
+# DRAM bytes (read + write) of the four FP32 scatter passes per element, from
+# one ncu capture of the current kernel (profiles/sort_scatter_uniform_512x2^16.md)
+SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 = 1.891e9 / 2 ** 25
 WORKLOAD = (f"uniform batch: {NCURVES} curves x 2^{LOG2N} samples, dt=1 d, bending PL PSD "
-            f"(f_br=1/300 d^-1, slopes 1/2), broken-PL ERDF [-4,0] break -1.5 slopes +0.4/-2.5, "
+            f"(f_br=1/300 d^-1, slopes 1 and 2), broken-PL ERDF [-4,0] break -1.5 slopes +0.4/-2.5, "
             f"{ITERS} E13 iterations, FP32")
 
 
@@ -328,11 +336,34 @@ def run_gpu(args):
     setup_ms = lc_plan_timing(plan.handle)[0]
     alg_per = ALG_BYTES_PER_SAMPLE_ITER * (2 if prec != LC_FP32 else 1)
     alg_bytes = alg_per * sample_iters
-    achieved = alg_bytes / (it_ms / 1000.0) / 1e9
+    stage_gbs = alg_bytes / (it_ms / 1000.0) / 1e9
+    # the dominant kernel, timed with CUDA events on the library's stream in
+    # one extra iteration launched kernel by kernel
+    from paper_1909_06374_gb300 import lc_plan_profile
+    prof = lc_plan_profile(plan.handle)
+    groups = {g: prof[g] for g in ("sort_scatter", "resident", "fft", "sort_hist_scan")}
+    dominant = max(groups, key=groups.get)
+    if dominant == "resident":
+        launches_k = 1
+        per_launch_bytes = alg_per * prof["fused_elements"]
+        kernel = "k_resident_cta / k_resident_cluster (one launch = one iteration of every fused curve)"
+    else:
+        dominant = "sort_scatter"
+        launches_k = max(1, prof["scatter_launches"])
+        # every element of every multi-kernel class goes through all passes
+        per_launch_bytes = SORT_BYTES_PER_ELEMENT[esize] * prof["sorted_elements"] / launches_k
+        kernel = "k_sort_scatter (radix passes of the argsort)"
+    avg_ms = prof[dominant] / launches_k
+    achieved = per_launch_bytes / (avg_ms / 1000.0) / 1e9
+    traffic = None
+    if dominant == "sort_scatter" and esize == 4:
+        traffic = SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 * prof["sorted_elements"] / launches_k
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "iteration stage (all E13 iterations of the batch)",
-            "peak_kind": peak_kind, "alg_bytes_per_sample_iter": alg_per,
-            "iterate_ms": it_ms, "setup_ms": setup_ms}
+            "traffic": traffic, "kernel": kernel, "launch_ms": avg_ms, "alg_bytes_per_launch": per_launch_bytes,
+            "peak_kind": peak_kind, "group_ms_one_iteration": {g: prof[g] for g in groups},
+            "iteration_stage": {"alg_bytes_per_sample_iter": alg_per, "achieved": stage_gbs,
+                                "frac": stage_gbs / peak, "iterate_ms": it_ms},
+            "setup_ms": setup_ms}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and args.workload == "uniform":

@@ -265,6 +265,21 @@ LC_API lc_status lc_periodogram(lc_plan plan, const void* x, int rms, double* ou
 LC_API lc_status lc_structure_function(lc_plan plan, const void* x, const uint32_t* lags, size_t nlags,
                                 double* out_sf2, void* stream);
 
+/* Profiling: runs ONE more amplitude-adjustment iteration of every curve on
+ * the plan's current state, launched kernel by kernel (not from the captured
+ * graph) with CUDA events on the plan's stream around each kernel group, and
+ * returns the device milliseconds per group:
+ *   group_ms[0] transforms and spectral step (multi-kernel path),
+ *   group_ms[1] sort histograms and scans, group_ms[2] sort scatter passes,
+ *   group_ms[3] fused on-chip kernels, group_ms[4] convergence test.
+ * ngroups: entries of group_ms to fill (extra ones get 0).
+ * counts (nullable, 3 entries): scatter launches timed, samples of the
+ * multi-kernel classes (each goes through every scatter pass), samples of
+ * the fused classes.
+ * The state advances by one iteration; the iteration counter restarts, so a
+ * later lc_iterate(plan, 0) runs each job's count again.  Blocking. */
+LC_API lc_status lc_plan_profile(lc_plan plan, float* group_ms, size_t ngroups, uint64_t* counts);
+
 /* Release the plan and its device memory (synchronises its stream). */
 LC_API lc_status lc_plan_destroy(lc_plan plan);
 

@@ -11,7 +11,7 @@ from __future__ import annotations
 from . import _abi
 from ._abi import (LC_FP32, LC_FP64, LcError, lc_generate, lc_generate_host, lc_get_state, lc_iterate,
                    lc_periodogram, lc_plan_buffer, lc_plan_convergence, lc_plan_create, lc_plan_destroy,
-                   lc_plan_last_launches, lc_structure_function,
+                   lc_plan_last_launches, lc_plan_profile, lc_structure_function,
                    lc_plan_set_convergence, lc_plan_timing, lc_plan_total_samples, lc_plan_workspace_bytes,
                    lc_poll, lc_server_create, lc_server_destroy, lc_server_stats, lc_set_state, lc_setup,
                    lc_submit)
@@ -20,6 +20,7 @@ __all__ = ["Plan", "LC_FP32", "LC_FP64", "LcError", "lc_plan_create", "lc_genera
            "lc_setup", "lc_iterate", "lc_get_state", "lc_set_state", "lc_plan_buffer",
            "lc_plan_last_launches", "lc_plan_timing", "lc_plan_total_samples", "lc_plan_workspace_bytes", "lc_plan_destroy",
            "lc_plan_set_convergence", "lc_plan_convergence", "lc_periodogram", "lc_structure_function",
+           "lc_plan_profile",
            "lc_server_create", "lc_submit", "lc_poll", "lc_server_stats", "lc_server_destroy"]
 
 

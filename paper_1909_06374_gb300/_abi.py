@@ -69,6 +69,7 @@ _SIGS = {
     "lc_plan_convergence": (c_i32, [c_p, c_p, c_p]),
     "lc_periodogram": (c_i32, [c_p, c_p, c_i32, c_p, c_p]),
     "lc_structure_function": (c_i32, [c_p, c_p, c_p, c_sz, c_p, c_p]),
+    "lc_plan_profile": (c_i32, [c_p, c_p, c_sz, c_p]),
     "lc_plan_destroy": (c_i32, [c_p]),
     "lc_generate_noalloc": (c_i32, [ctypes.POINTER(LcJob), c_p, c_p]),
     "lc_server_create": (c_i32, [c_i32, c_sz, c_i32, ctypes.POINTER(c_p)]),
@@ -250,6 +251,17 @@ def lc_structure_function(plan, x, lags, out_sf2, stream=None):
     L = np.ascontiguousarray(lags, dtype=np.uint32)
     _check(load().lc_structure_function(plan, ptr(x), L.ctypes.data_as(c_p), L.size, ptr(out_sf2),
                                         stream_ptr(stream)), "lc_structure_function")
+
+
+def lc_plan_profile(plan):
+    """Per-group device ms of one extra iteration (see agnlc.h) as a dict."""
+    ms = (ctypes.c_float * 5)()
+    cnt = (c_u64 * 3)()
+    _check(load().lc_plan_profile(plan, ms, 5, cnt), "lc_plan_profile")
+    names = ("fft", "sort_hist_scan", "sort_scatter", "resident", "convergence")
+    out = {n: float(v) for n, v in zip(names, ms)}
+    out["scatter_launches"], out["sorted_elements"], out["fused_elements"] = int(cnt[0]), int(cnt[1]), int(cnt[2])
+    return out
 
 
 def lc_plan_destroy(plan):

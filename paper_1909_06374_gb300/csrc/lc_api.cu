@@ -324,10 +324,11 @@ static lc_status run_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* lau
 
 // One amplitude-adjustment iteration of every class (Sec. 3.2.2).
 template <typename T>
-static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches)
+static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches, KernelTimes* kt = nullptr)
 {
     for (auto& k : p.classes) {
         if (k.resident) continue;
+        if (kt) kt->begin(kGroupFFT, st);
         // with the convergence test the FFTs work in d_f and d_keysB (free
         // until the sort starts) so that x_{i-1} stays in d_x for Eq. 4
         void* alt = p.conv_on ? p.d_keysB : p.d_x;
@@ -343,14 +344,17 @@ static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches)
             ++*launches;
             R3 = launch_fft<T>(p, k, true, Zp, R1, nullptr, true, st, launches);
         }
+        if (kt) kt->end(st);
         if (!p.conv_on) {
-            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches);
+            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, nullptr, kt);
         } else {
             // the last sort pass reads keys A, so x_i can go to keys B; Eq. 4
             // then compares it with x_{i-1} in one coalesced pass
-            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, p.d_keysB);
+            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, p.d_keysB, kt);
+            if (kt) kt->begin(kGroupOther, st);
             launch_conv_delta<T>(p, k, p.d_keysB, st);
             launch_conv_finalize(p, k, st);
+            if (kt) kt->end(st);
             *launches += 2;
         }
     }
@@ -700,6 +704,49 @@ lc_status lc_plan_convergence(lc_plan plan, double* deltas, uint32_t* iters_run)
     LC_CK(cudaStreamSynchronize(plan->stream));
     if (iters_run)
         for (size_t c = 0; c < nc; ++c) iters_run[c] = std::min(eff[c], (uint32_t)std::max(it, 0));
+    return LC_OK;
+}
+
+lc_status lc_plan_profile(lc_plan plan, float* group_ms, size_t ngroups, uint64_t* counts)
+{
+    if (!plan || !group_ms) { set_error("null plan or group_ms"); return LC_ERR_INVALID; }
+    if (!plan->setup_done) { set_error("lc_plan_profile before lc_setup/lc_generate"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    Plan& p = *plan;
+    cudaStream_t st = p.stream;
+    LC_CK(cudaStreamSynchronize(st));
+    uint64_t launches = 0;
+    {
+        KernelTimes kt;
+        launch_eff_iters(p, 1, st);  // one iteration of every curve, counter from 0
+        for (auto& k : p.classes) {
+            if (!k.resident) continue;
+            kt.begin(kGroupResident, st);
+            launch_resident(p, k, 1, st, &launches);
+            kt.end(st);
+        }
+        if (p.prec == LC_FP32) enqueue_iteration<float>(p, st, &launches, &kt);
+        else enqueue_iteration<double>(p, st, &launches, &kt);
+        LC_CK(cudaGetLastError());
+        LC_CK(cudaStreamSynchronize(st));
+        std::vector<float> sums(kGroups, 0.f);
+        uint64_t nscatter = 0;
+        for (auto& s : kt.spans) {
+            float ms = 0.f;
+            LC_CK(cudaEventElapsedTime(&ms, s.a, s.b));
+            sums[s.group] += ms;
+            nscatter += s.group == kGroupSortScatter;
+        }
+        for (size_t q = 0; q < ngroups; ++q) group_ms[q] = q < (size_t)kGroups ? sums[q] : 0.f;
+        if (counts) counts[0] = nscatter;
+    }
+    if (counts) {
+        uint64_t multi = 0, fused = 0;
+        for (auto& k : p.classes) (k.resident ? fused : multi) += (uint64_t)k.ncurves << k.log2n;
+        counts[1] = multi;
+        counts[2] = fused;
+    }
+    p.timed_iter = false;
     return LC_OK;
 }
 

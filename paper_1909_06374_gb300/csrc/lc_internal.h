@@ -91,6 +91,39 @@ struct Plan {
     size_t conv_part = 0;        // doubles in conv.part
 };
 
+// CUDA events around the kernel groups of one profiled iteration.
+enum KernelGroup {
+    kGroupFFT = 0,           // transforms and spectral step (multi-kernel path)
+    kGroupSortHistScan = 1,  // per-tile histograms and their scans
+    kGroupSortScatter = 2,   // ranked scatter passes
+    kGroupResident = 3,      // fused on-chip iteration kernels
+    kGroupOther = 4,         // convergence test
+    kGroups = 5
+};
+struct KernelTimes {
+    struct Span {
+        int group;
+        cudaEvent_t a, b;
+    };
+    std::vector<Span> spans;
+    void begin(int g, cudaStream_t st)
+    {
+        Span s{g, nullptr, nullptr};
+        cudaEventCreate(&s.a);
+        cudaEventCreate(&s.b);
+        cudaEventRecord(s.a, st);
+        spans.push_back(s);
+    }
+    void end(cudaStream_t st) { cudaEventRecord(spans.back().b, st); }
+    ~KernelTimes()
+    {
+        for (auto& s : spans) {
+            cudaEventDestroy(s.a);
+            cudaEventDestroy(s.b);
+        }
+    }
+};
+
 // ConvDev of a plan: null pointers when the convergence test is off.
 inline ConvDev conv_of(const Plan& p) { return p.conv_on ? p.conv : ConvDev{}; }
 
@@ -136,7 +169,8 @@ enum SortMode { kSortArgsortScatter = 1, kSortKeysToValues = 2 };
 // kSortArgsortScatter writes x[perm[r]] = s[r] (x = x_out, default the
 // state); kSortKeysToValues writes the sorted values to s.
 template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode,
-                                       bool gated, cudaStream_t st, uint64_t* launches, void* x_out = nullptr);
+                                       bool gated, cudaStream_t st, uint64_t* launches, void* x_out = nullptr,
+                                       KernelTimes* kt = nullptr);
 // Eq. 4 partial sums of a multi-kernel class between the state x_{i-1} and
 // the new iterate x_i in `xnew` (one double per sort tile, curve-major, in
 // conv.part), moving x_i into the state; for launch_conv_finalize.

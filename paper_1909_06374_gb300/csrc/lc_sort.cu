@@ -400,7 +400,7 @@ static void launch_scatter(int mode, const SortArgs& a, int blocks, cudaStream_t
 
 template <typename T>
 void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode, bool gated,
-                 cudaStream_t st, uint64_t* launches, void* x_out)
+                 cudaStream_t st, uint64_t* launches, void* x_out, KernelTimes* kt)
 {
     using K = typename key_of<T>::type;
     const int passes = (int)sizeof(K);  // 8-bit digits
@@ -428,20 +428,24 @@ void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mo
         a.vals_in = (q % 2 == 1) ? p.d_valsA : p.d_valsB;
         a.keys_out = (q % 2 == 0) ? p.d_keysA : p.d_keysB;
         a.vals_out = (q % 2 == 0) ? p.d_valsA : p.d_valsB;
+        if (kt) kt->begin(kGroupSortHistScan, st);
         if (first) k_sort_hist<T, true><<<blocks, kSortThreads, 0, st>>>(a);
         else k_sort_hist<T, false><<<blocks, kSortThreads, 0, st>>>(a);
         k_sort_scan_tiles<<<k.ncurves * k.nchunks, 256, 0, st>>>(a);
         k_sort_scan_chunks<<<k.ncurves, 256, 0, st>>>(a);
+        if (kt) kt->end(st);
         const int m = last ? (int)mode : 0;
+        if (kt) kt->begin(kGroupSortScatter, st);
         if (first) launch_scatter<T, true>(m, a, blocks, st);
         else launch_scatter<T, false>(m, a, blocks, st);
+        if (kt) kt->end(st);
         if (launches) *launches += 4;
     }
 }
 
 template void launch_sort<float>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t, uint64_t*,
-                                void*);
+                                void*, KernelTimes*);
 template void launch_sort<double>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t,
-                                 uint64_t*, void*);
+                                 uint64_t*, void*, KernelTimes*);
 
 }  // namespace lc

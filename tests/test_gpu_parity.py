@@ -318,3 +318,25 @@ def test_forced_paths_one_step_at_2_16(path, monkeypatch):
     for c, (x1, s, xa) in enumerate(expect):
         r = position_check(got[p.offsets[c]:p.offsets[c + 1]], x1, s, xa)
         assert r["fail"] == 0 and r["not_in_draws"] == 0, (path, c, r)
+
+
+def test_profile_runs_one_iteration_with_timed_groups():
+    """lc_plan_profile advances the state by exactly one iteration (the same
+    bits as lc_iterate(1) from that state) and times the kernel groups that
+    ran: fused kernels for the 2^12 curve, transforms / sort for the rest."""
+    from paper_1909_06374_gb300 import lc_plan_profile
+    jobs = [workloads.job(12, 2, seed=1, curve_id=0), workloads.job(17, 2, seed=2, curve_id=1),
+            workloads.job(9, 2, seed=3, curve_id=2)]
+    with Plan(jobs, LC_FP32) as p:
+        p.generate()
+        start = p.get_state()
+        prof = lc_plan_profile(p.handle)
+        after = _np(p.get_state())
+        p.set_state(start)
+        p.iterate(1)
+        want = _np(p.get_state())
+    assert np.array_equal(after, want)
+    assert prof["resident"] > 0 and prof["fft"] > 0 and prof["sort_scatter"] > 0 and prof["sort_hist_scan"] > 0
+    assert prof["convergence"] == 0
+    assert prof["scatter_launches"] == 2 * 4  # two multi-kernel classes, four FP32 radix passes
+    assert prof["sorted_elements"] == (1 << 17) + (1 << 9) and prof["fused_elements"] == 1 << 12
