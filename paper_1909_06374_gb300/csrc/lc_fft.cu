@@ -43,26 +43,31 @@ struct SmemTw {
     }
 };
 
-// Fills the tables at `mem` (3 x 512 entries) for a length-M transform;
-// ends with a block barrier.
+__host__ __device__ constexpr int smem_tw_entries(int log2M)
+{
+    return kTwLevel + (log2M >= 18 ? kTwLevel : (1 << (log2M - 9))) + (log2M > 18 ? (1 << (log2M - 18)) : 0);
+}
+
+// Fills the tables at `mem` (smem_tw_entries(log2M) entries: 512, then the
+// 2^(log2M-9) or 512 of the second level, then those of the third) for a
+// length-M transform; ends with a block barrier.
 template <typename T>
 __device__ __forceinline__ SmemTw<T> build_smem_tw(cplx<T>* mem, const cplx<T>* __restrict__ rt, int log2M)
 {
     const uint64_t M = 1ull << log2M;
     SmemTw<T> tw;
     tw.t0 = mem;
-    tw.t1 = mem + kTwLevel;
-    tw.t2 = mem + 2 * kTwLevel;
     tw.three = log2M > 18;
     const int n1 = log2M >= 18 ? kTwLevel : (1 << (log2M - 9));
     const int n2 = log2M > 18 ? (1 << (log2M - 18)) : 0;
+    tw.t1 = mem + kTwLevel;
+    tw.t2 = mem + kTwLevel + n1;
     for (int x = threadIdx.x; x < kTwLevel + n1 + n2; x += blockDim.x) {
         uint64_t e;
         if (x < kTwLevel) e = (uint64_t)x;
         else if (x < kTwLevel + n1) e = (uint64_t)(x - kTwLevel) << 9;
         else e = (uint64_t)(x - kTwLevel - n1) << 18;
-        const int slot = x < kTwLevel + n1 ? x : 2 * kTwLevel + (x - kTwLevel - n1);
-        mem[slot] = twiddle_M<T>(rt, e, M);
+        mem[x] = twiddle_M<T>(rt, e, M);
     }
     __syncthreads();
     return tw;
@@ -144,41 +149,72 @@ __global__ void __launch_bounds__(256) k_fft_pass(const PassArgs a)
 // of kTileCols adjacent columns i0..i0+15 of one curve: the tile loads
 // u_r[i] = z[i + r M/R] (coalesced runs of 16 columns), applies W_{Rp}^{r k},
 // takes the R-point DFT of every column by radix-16 Stockham sub-passes in
-// shared memory (rows padded to 17 elements), and stores
+// one shared-memory buffer (rows padded to 17 elements; each sub-pass reads
+// its butterflies into registers, then overwrites the buffer), and stores
 // y[(i-k)R + k + q p] (coalesced along i, or along q when p = 1).
 constexpr int kTileCols = 16;
 constexpr int kTileStride = kTileCols + 1;
 
-template <typename T, int Q, bool INV>
-__device__ __forceinline__ void tile_subpass(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int LR,
-                                             int log2p2, const SmemTw<T>& tw, int log2M)
+template <typename T, int Q, bool INV, int LR>
+__device__ __forceinline__ void tile_subpass(cplx<T>* __restrict__ buf, int log2p2, const SmemTw<T>& tw, int log2M)
 {
     using V = cplx<T>;
     constexpr int LQ = ilog2c(Q);
-    const int R = 1 << LR;
-    const int nbq = R >> LQ;                 // butterflies per column
+    constexpr int R = 1 << LR;
+    constexpr int nbq = R >> LQ;                 // butterflies per column
+    constexpr int NB = nbq * kTileCols;          // butterflies of the tile
+    constexpr int BPT = (NB + 255) / 256;        // per thread
     const int p2 = 1 << log2p2;
-    for (int b = threadIdx.x; b < nbq * kTileCols; b += 256) {
-        const int j = b & (kTileCols - 1);
-        const int i2 = b >> 4;
-        const int k2 = i2 & (p2 - 1);
-        V u[Q];
+    V u[BPT][Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) u[q] = in[(i2 + q * nbq) * kTileStride + j];
-        if (p2 > 1) {
-            // W_{Q p2}^{q k2} = W_M^{q k2 M/(Q p2)}
-            const uint64_t step = (uint64_t)k2 << (log2M - LQ - log2p2);
+    for (int bi = 0; bi < BPT; ++bi) {
+        const int b = threadIdx.x + bi * 256;
+        if (NB % 256 == 0 || b < NB) {
+            const int j = b & (kTileCols - 1), i2 = b >> 4;
 #pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                V w = tw((uint64_t)q * step);
-                if (INV) w.y = -w.y;
-                u[q] = cmul(u[q], w);
-            }
+            for (int q = 0; q < Q; ++q) u[bi][q] = buf[(i2 + q * nbq) * kTileStride + j];
         }
-        dft_regs<T, Q, INV>(u);
-        const int jo = ((i2 - k2) << LQ) + k2;
+    }
+    __syncthreads();
 #pragma unroll
-        for (int q = 0; q < Q; ++q) out[(jo + q * p2) * kTileStride + j] = u[q];
+    for (int bi = 0; bi < BPT; ++bi) {
+        const int b = threadIdx.x + bi * 256;
+        if (NB % 256 == 0 || b < NB) {
+            const int j = b & (kTileCols - 1), i2 = b >> 4;
+            const int k2 = i2 & (p2 - 1);
+            if (p2 > 1) {
+                // W_{Q p2}^{q k2} = W_M^{q k2 M/(Q p2)}
+                const uint64_t step = (uint64_t)k2 << (log2M - LQ - log2p2);
+#pragma unroll
+                for (int q = 1; q < Q; ++q) {
+                    V w = tw((uint64_t)q * step);
+                    if (INV) w.y = -w.y;
+                    u[bi][q] = cmul(u[bi][q], w);
+                }
+            }
+            dft_regs<T, Q, INV>(u[bi]);
+            const int jo = ((i2 - k2) << LQ) + k2;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) buf[(jo + q * p2) * kTileStride + j] = u[bi][q];
+        }
+    }
+}
+
+// All radix-2^LR sub-passes of one tile, in place in `buf`: a radix-2/4/8
+// sub-pass for LR mod 4, then radix-16 ones.  Ends with a block barrier.
+template <typename T, bool INV, int LR>
+__device__ __forceinline__ void tile_dft(cplx<T>* __restrict__ buf, const SmemTw<T>& tw, int log2M)
+{
+    constexpr int rem = LR & 3;
+    int log2p2 = 0;
+    if (rem) {
+        tile_subpass<T, (1 << (rem ? rem : 1)), INV, LR>(buf, 0, tw, log2M);
+        __syncthreads();
+        log2p2 = rem;
+    }
+    for (; log2p2 < LR; log2p2 += 4) {
+        tile_subpass<T, 16, INV, LR>(buf, log2p2, tw, log2M);
+        __syncthreads();
     }
 }
 
@@ -189,8 +225,7 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
     constexpr int R = 1 << LR;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     V* b0 = (V*)tile_smem;
-    V* b1 = b0 + R * kTileStride;
-    V* twm = b1 + R * kTileStride;
+    V* twm = b0 + R * kTileStride;
     const uint32_t log2nb = a.log2M - LR;
     const int tpc = 1 << (log2nb - 4);       // tiles per curve (nb >= 16)
     const int ci = blockIdx.x / tpc;
@@ -226,21 +261,8 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
         b0[r * kTileStride + j] = x;
     }
     __syncthreads();
-    V* in = b0;
-    V* out = b1;
-    int log2p2 = 0;
-    constexpr int rem = LR & 3;
-    if (rem) {
-        tile_subpass<T, (1 << (rem ? rem : 1)), INV>(in, out, LR, 0, tw, a.log2M);
-        __syncthreads();
-        log2p2 = rem;
-        V* t = in; in = out; out = t;
-    }
-    for (; log2p2 < LR; log2p2 += 4) {
-        tile_subpass<T, 16, INV>(in, out, LR, log2p2, tw, a.log2M);
-        __syncthreads();
-        V* t = in; in = out; out = t;
-    }
+    tile_dft<T, INV, LR>(b0, tw, (int)a.log2M);
+    const V* in = b0;
     if (p >= (uint64_t)kTileCols) {
         for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
             const int q = idx >> 4, j = idx & (kTileCols - 1);
@@ -428,8 +450,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     constexpr int R = 1 << LR;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     V* b0 = (V*)tile_smem;
-    V* b1 = b0 + R * kTileStride;
-    V* twm = b1 + R * kTileStride;
+    V* twm = b0 + R * kTileStride;
     const uint32_t log2p = a.log2M - LR;
     const uint64_t p = 1ull << log2p;
     const int tpc = (int)(p >> 4);
@@ -466,21 +487,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
         b0[r * kTileStride + j] = cmul(v[e], tw((uint64_t)r * column(j)));
     }
     __syncthreads();
+    tile_dft<T, false, LR>(b0, tw, (int)a.log2M);
     V* in = b0;
-    V* out = b1;
-    int log2p2 = 0;
-    constexpr int rem = LR & 3;
-    if (rem) {
-        tile_subpass<T, (1 << (rem ? rem : 1)), false>(in, out, LR, 0, tw, a.log2M);
-        __syncthreads();
-        log2p2 = rem;
-        V* t = in; in = out; out = t;
-    }
-    for (; log2p2 < LR; log2p2 += 4) {
-        tile_subpass<T, 16, false>(in, out, LR, log2p2, tw, a.log2M);
-        __syncthreads();
-        V* t = in; in = out; out = t;
-    }
     // spectral step on the conjugate pairs, in place: in[q][j] = Z_{column(j) + q p}
     for (int idx = threadIdx.x; idx < R * 8; idx += 256) {
         const int q = idx >> 3, j = idx & 7;
@@ -511,18 +519,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     }
     __syncthreads();
     // inverse first pass (span 1: no input twiddle)
-    log2p2 = 0;
-    if (rem) {
-        tile_subpass<T, (1 << (rem ? rem : 1)), true>(in, out, LR, 0, tw, a.log2M);
-        __syncthreads();
-        log2p2 = rem;
-        V* t = in; in = out; out = t;
-    }
-    for (; log2p2 < LR; log2p2 += 4) {
-        tile_subpass<T, 16, true>(in, out, LR, log2p2, tw, a.log2M);
-        __syncthreads();
-        V* t = in; in = out; out = t;
-    }
+    tile_dft<T, true, LR>(b0, tw, (int)a.log2M);
     for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
         const int j = idx >> LR, q = idx & (R - 1);
         dst[(column(j) << LR) + q] = in[q * kTileStride + j];
@@ -568,9 +565,9 @@ static void launch_pass(int R, const PassArgs& a, uint64_t work, cudaStream_t st
 }
 
 // Tile passes for a length-2^log2M transform (log2M >= 12): as few passes as
-// possible with at most 9 (float) or 8 (double) bits each -- the tile of
-// 2 x 2^bits x 17 elements must fit in shared memory -- bits spread evenly,
-// so every pass has between 5 and 9 bits.
+// possible with at most 9 (float) or 8 (double) bits each -- a tile of
+// 2^bits x 17 elements in shared memory with room for two or more resident
+// blocks per SM -- bits spread evenly, so every pass has between 5 and 9 bits.
 std::vector<int> tile_radices(uint32_t log2m, bool fp64)
 {
     const int maxb = fp64 ? 8 : 9;
@@ -583,7 +580,7 @@ std::vector<int> tile_radices(uint32_t log2m, bool fp64)
 template <typename T, int LR, bool INV>
 static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
 {
-    const size_t smem = ((size_t)2 * ((size_t)1 << LR) * kTileStride + 3 * kTwLevel) * sizeof(cplx<T>);
+    const size_t smem = (((size_t)1 << LR) * kTileStride + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
     cudaFuncSetAttribute(k_fft_tile<T, LR, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fft_tile<T, LR, INV><<<blocks, 256, smem, st>>>(a);
 }
@@ -718,7 +715,7 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
     a.in = cur; a.out = nxt; a.log2p = log2p;
     {
         const int blocks = k.ncurves << (a.log2M - LR - 4);
-        const size_t smem = ((size_t)2 * ((size_t)1 << LR) * kTileStride + 3 * kTwLevel) * sizeof(cplx<T>);
+        const size_t smem = (((size_t)1 << LR) * kTileStride + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
         switch (LR) {
 #define LC_FUSED_CASE(L)                                                                                   \
     case L:                                                                                                \

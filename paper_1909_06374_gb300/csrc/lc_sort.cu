@@ -46,31 +46,98 @@ __device__ __forceinline__ bool curve_active(const SortArgs& a, int c)
     return !a.d_iter || (uint32_t)(*a.d_iter) < a.eff_iters[c];
 }
 
-template <typename T, bool FIRST>
-__device__ __forceinline__ typename key_of<T>::type load_key(const SortArgs& a, uint64_t idx)
+// Key bits of a value stored as T, reinterpreted from the key word.
+__device__ __forceinline__ float value_bits(uint32_t b) { return __uint_as_float(b); }
+__device__ __forceinline__ double value_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Exclusive scan of v over the 256 threads of a block (all threads call it).
+__device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t v, uint32_t* wsum)
 {
-    using K = typename key_of<T>::type;
-    if (FIRST) return order_key(((const T*)a.src)[idx]);
-    return ((const K*)a.keys_in)[idx];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int q = 0; q < w; ++q) woff += wsum[q];
+    return woff + incl - v;
 }
 
+// Curve ci of at most kScanChunk tiles: tile histograms -> exclusive tile
+// prefixes in place (digit threadIdx.x), digit bases -> cbase.
+__device__ __forceinline__ void scan_curve(const SortArgs& a, int ci, uint32_t* wsum)
+{
+    const int tid = threadIdx.x;
+    uint32_t* hrow = a.hist + (size_t)ci * a.tpc * 256;
+    uint32_t v[kScanChunk];
+#pragma unroll
+    for (int u = 0; u < kScanChunk; ++u) v[u] = u < a.tpc ? __ldcg(&hrow[(size_t)u * 256 + tid]) : 0u;
+    uint32_t run = 0;
+#pragma unroll
+    for (int u = 0; u < kScanChunk; ++u) {
+        if (u < a.tpc) hrow[(size_t)u * 256 + tid] = run;
+        run += v[u];
+    }
+    a.cbase[(size_t)ci * 256 + tid] = block_exclusive_scan256(run, wsum);
+}
+
+// Per-tile 8-bit digit histogram: 16-byte loads, all of a thread's loads in
+// flight before the counting, per-warp counters.
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const SortArgs a)
 {
+    using K = typename key_of<T>::type;
+    constexpr int EPV = 16 / (int)sizeof(K);                  // keys per 16-byte load
+    constexpr int VPT = kSortTile / EPV / kSortThreads;       // loads per thread, full tile
     const int ci = blockIdx.x / a.tpc;
     const int t = blockIdx.x % a.tpc;
     const int c = a.cls_curves[ci];
     if (!curve_active(a, c)) return;
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
+    __shared__ uint32_t h[kSortWarps][256];
+    const int tid = threadIdx.x, warp = tid >> 5;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) h[w][tid] = 0;
     const uint64_t base = a.curves[c].off + (uint64_t)t * a.tile_len;
-    for (int e = threadIdx.x; e < a.tile_len; e += kSortThreads) {
-        const auto key = load_key<T, FIRST>(a, base + e);
-        atomicAdd(&h[(uint32_t)(key >> a.shift) & 255u], 1u);
+    const uint4* __restrict__ src = (const uint4*)((const K*)(FIRST ? a.src : a.keys_in) + base);
+    const int nvec = a.tile_len / EPV;
+    uint4 q[VPT];
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+        const int v = tid + e * kSortThreads;
+        if (v < nvec) q[e] = src[v];
     }
     __syncthreads();
-    a.hist[((size_t)ci * a.tpc + t) * 256 + threadIdx.x] = h[threadIdx.x];
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+        if (tid + e * kSortThreads < nvec) {
+            const K* kk = (const K*)&q[e];
+#pragma unroll
+            for (int j = 0; j < EPV; ++j) {
+                const K key = FIRST ? order_key(value_bits(kk[j])) : kk[j];
+                atomicAdd(&h[warp][(uint32_t)(key >> a.shift) & 255u], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) cnt += h[w][tid];
+    a.hist[((size_t)ci * a.tpc + t) * 256 + tid] = cnt;
+}
+
+// One block per curve of at most kScanChunk tiles: the histograms become tile
+// prefixes and the digit bases go to cbase (k_sort_scan_tiles and
+// k_sort_scan_chunks in one launch).
+__global__ void __launch_bounds__(256) k_sort_scan_curve(const SortArgs a)
+{
+    const int ci = blockIdx.x;
+    if (!curve_active(a, a.cls_curves[ci])) return;
+    __shared__ uint32_t wsum[kSortWarps];
+    scan_curve(a, ci, wsum);
 }
 
 // Exclusive prefix of every digit over the tiles of one chunk (in place) and
@@ -143,24 +210,29 @@ __device__ __forceinline__ uint32_t peers8(uint32_t d)
 constexpr int kSlots = kSortTile / kSortThreads;  // elements per thread of a full tile
 
 // Stable scatter of one tile: the tile's elements are ranked in shared memory
-// (warp w owns elements [w T/8, (w+1) T/8), lane-striped; ballot multisplit
-// within the warp, per-warp digit counts, one block scan), placed in a
-// digit-sorted shared copy, and written out run by run, so that consecutive
-// threads write consecutive addresses of a digit's output range; digit d's
-// run starts at gb[d] within the curve.
-// MODE 0: sorted (key, position) pairs; kSortArgsortScatter: x[position] =
-// s[rank]; kSortKeysToValues: s[rank] = value.
-// Expects wcnt zeroed and gb set (after a block barrier); returns the tile's
-// count of digit threadIdx.x.  Ends with a block barrier.
+// (warp w owns elements [w T/8, (w+1) T/8), lane-striped; ballot/match
+// multisplit, per-warp digit counts, one block scan).  MODE 0: the tile is
+// placed digit-sorted in shared memory and each digit's run written out with
+// coalesced stores of (key, position) pairs, digit d's run starting at gb[d]
+// within the curve.  kSortKeysToValues: the same with s[rank] = value.
+// kSortArgsortScatter (the last pass of an argsort): every element's rank in
+// the curve is gb[d] + (count of d in earlier warps) + (rank in its warp), and
+// the element writes x[position] = s[rank] straight from registers (the
+// stores are scattered anyway), with no shared-memory placement.
+// Expects wcnt zeroed and gb set (after a block barrier).  Ends with a block
+// barrier.
 template <typename T, bool FIRST, int MODE>
-__device__ __forceinline__ uint32_t sort_tile(const SortArgs& a, const void* kin, const uint32_t* vin, void* kout,
-                                              uint32_t* vout, int shift, uint64_t off, uint32_t e0, int tl,
-                                              typename key_of<T>::type* sk, uint32_t* sv,
-                                              uint32_t (*wcnt)[256], uint32_t* ldstart, const uint32_t* gb,
-                                              uint32_t* wsum)
+__device__ __forceinline__ void sort_tile(const SortArgs& a, const void* kin, const uint32_t* vin, void* kout,
+                                          uint32_t* vout, int shift, uint64_t off, uint32_t e0, int tl,
+                                          typename key_of<T>::type* sk, uint32_t* sv,
+                                          uint32_t (*wcnt)[256], uint32_t* ldstart, uint32_t* gb,
+                                          uint32_t* wsum)
 {
     using K = typename key_of<T>::type;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const T* __restrict__ src_t = (const T*)a.src + off + e0;
+    const K* __restrict__ src_k = (const K*)kin + off + e0;
+    const uint32_t* __restrict__ src_v = vin + off + e0;
     const int EW = (tl + kSortWarps - 1) / kSortWarps;  // elements per warp
     const uint32_t lt = (1u << lane) - 1u;
     K key[kSlots];
@@ -178,8 +250,8 @@ __device__ __forceinline__ uint32_t sort_tile(const SortArgs& a, const void* kin
         K k = 0;
         uint32_t v = 0, d = 256u + lane;          // empty slots never match a digit
         if (valid) {
-            k = FIRST ? order_key(((const T*)a.src)[off + e0 + el]) : ((const K*)kin)[off + e0 + el];
-            v = FIRST ? e0 + el : vin[off + e0 + el];
+            k = FIRST ? order_key(src_t[el]) : src_k[el];
+            v = FIRST ? e0 + el : src_v[el];
             d = (uint32_t)(k >> shift) & 255u;
         }
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
@@ -200,7 +272,7 @@ __device__ __forceinline__ uint32_t sort_tile(const SortArgs& a, const void* kin
         rk[e] = valid ? base + below : 0xffffffffu;
     }
     __syncthreads();
-    // per-digit prefix over warps (in place) and the tile's digit starts
+    // per-digit prefix over warps (in place)
     uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
@@ -208,6 +280,26 @@ __device__ __forceinline__ uint32_t sort_tile(const SortArgs& a, const void* kin
         wcnt[w][tid] = tot;
         tot += v;
     }
+    if (MODE == kSortArgsortScatter) {
+        __syncthreads();
+        // all loads of s before the thread's first store
+        const T* __restrict__ s_in = (const T*)a.s_in + off;
+        T* __restrict__ x_out = (T*)a.x_out + off;
+        T xn[kSlots];
+#pragma unroll
+        for (int e = 0; e < kSlots; ++e) {
+            if (rk[e] != 0xffffffffu) {
+                const uint32_t d = info[e] & 255u;
+                xn[e] = s_in[gb[d] + wcnt[warp][d] + rk[e]];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < kSlots; ++e)
+            if (rk[e] != 0xffffffffu) x_out[val[e]] = xn[e];
+        __syncthreads();
+        return;
+    }
+    // the tile's digit starts
     uint32_t incl = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -218,52 +310,34 @@ __device__ __forceinline__ uint32_t sort_tile(const SortArgs& a, const void* kin
     __syncthreads();
     uint32_t woff = 0;
     for (int q = 0; q < warp; ++q) woff += wsum[q];
-    ldstart[tid] = woff + incl - tot;
+    const uint32_t ls = woff + incl - tot;
+    ldstart[tid] = ls;
+    gb[tid] -= ls;  // from here on: output index of tile position i of digit d = gb[d] + i
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < kSlots; ++e) {
         if (rk[e] != 0xffffffffu) {
-            const uint32_t d = (uint32_t)(key[e] >> shift) & 255u;
+            const uint32_t d = info[e] & 255u;
             const uint32_t lp = ldstart[d] + wcnt[warp][d] + rk[e];
             sk[lp] = key[e];
             sv[lp] = val[e];
         }
     }
     __syncthreads();
-    if (MODE == kSortArgsortScatter) {
-        // every run read of s is issued before the thread's first store, so
-        // the loads overlap instead of waiting behind possibly aliasing stores
-        T xn[kSlots];
-        uint32_t pos[kSlots];
-#pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
-            const int i = tid + e * kSortThreads;
-            if (i < tl) {
-                const K k = sk[i];
-                const uint32_t d = (uint32_t)(k >> shift) & 255u;
-                const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
-                pos[e] = sv[i];
-                xn[e] = ((const T*)a.s_in)[off + dest];
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < kSlots; ++e)
-            if (tid + e * kSortThreads < tl) ((T*)a.x_out)[off + pos[e]] = xn[e];
-    } else {
-        for (int i = tid; i < tl; i += kSortThreads) {
-            const K k = sk[i];
-            const uint32_t d = (uint32_t)(k >> shift) & 255u;
-            const uint32_t dest = gb[d] + ((uint32_t)i - ldstart[d]);
-            if (MODE == 0) {
-                ((K*)kout)[off + dest] = k;
-                vout[off + dest] = sv[i];
-            } else {
-                ((T*)a.s_out)[off + dest] = key_value(k);
-            }
+    K* __restrict__ kdst = (K*)kout + off;
+    uint32_t* __restrict__ vdst = vout + off;
+    T* __restrict__ sdst = (T*)a.s_out + off;
+    for (int i = tid; i < tl; i += kSortThreads) {
+        const K k = sk[i];
+        const uint32_t dest = gb[(uint32_t)(k >> shift) & 255u] + (uint32_t)i;
+        if (MODE == 0) {
+            kdst[dest] = k;
+            vdst[dest] = sv[i];
+        } else {
+            sdst[dest] = key_value(k);
         }
     }
     __syncthreads();
-    return tot;
 }
 
 // One pass over one tile per block: the tile's output bases come from the
@@ -431,15 +505,19 @@ void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mo
         if (kt) kt->begin(kGroupSortHistScan, st);
         if (first) k_sort_hist<T, true><<<blocks, kSortThreads, 0, st>>>(a);
         else k_sort_hist<T, false><<<blocks, kSortThreads, 0, st>>>(a);
-        k_sort_scan_tiles<<<k.ncurves * k.nchunks, 256, 0, st>>>(a);
-        k_sort_scan_chunks<<<k.ncurves, 256, 0, st>>>(a);
+        if (k.nchunks == 1) {
+            k_sort_scan_curve<<<k.ncurves, 256, 0, st>>>(a);
+        } else {
+            k_sort_scan_tiles<<<k.ncurves * k.nchunks, 256, 0, st>>>(a);
+            k_sort_scan_chunks<<<k.ncurves, 256, 0, st>>>(a);
+        }
         if (kt) kt->end(st);
         const int m = last ? (int)mode : 0;
         if (kt) kt->begin(kGroupSortScatter, st);
         if (first) launch_scatter<T, true>(m, a, blocks, st);
         else launch_scatter<T, false>(m, a, blocks, st);
         if (kt) kt->end(st);
-        if (launches) *launches += 4;
+        if (launches) *launches += k.nchunks == 1 ? 3 : 4;
     }
 }
 
