@@ -146,23 +146,30 @@ __global__ void __launch_bounds__(256) k_fft_pass(const PassArgs a)
 }
 
 // One Stockham pass of radix R = 2^LR computed in shared memory over a tile
-// of kTileCols adjacent columns i0..i0+15 of one curve: the tile loads
-// u_r[i] = z[i + r M/R] (coalesced runs of 16 columns), applies W_{Rp}^{r k},
-// takes the R-point DFT of every column by radix-16 Stockham sub-passes in
-// one shared-memory buffer (rows padded to 17 elements; each sub-pass reads
-// its butterflies into registers, then overwrites the buffer), and stores
-// y[(i-k)R + k + q p] (coalesced along i, or along q when p = 1).
-constexpr int kTileCols = 16;
-constexpr int kTileStride = kTileCols + 1;
+// of C adjacent columns i0..i0+C-1 of one curve (C = tile_cols: R C = 4096
+// elements for FP32 and R <= 256, so that every radix-16 sub-pass gives each of the
+// 256 threads one butterfly): the tile loads u_r[i] = z[i + r M/R]
+// (coalesced runs of C columns), applies W_{Rp}^{r k}, takes the R-point DFT
+// of every column by radix-16 Stockham sub-passes in one shared-memory buffer
+// (rows padded to C+1 elements; each sub-pass reads its butterflies into
+// registers, then overwrites the buffer), and stores y[(i-k)R + k + q p]
+// (coalesced along i, or along q when p = 1).
+// (FP64 keeps C = 16: with its radices a span 1 < p < C would occur.)
+__host__ __device__ constexpr int tile_cols(int LR, int elem_bytes)
+{
+    return (LR >= 8 || elem_bytes > 8) ? 16 : (4096 >> LR);
+}
 
-template <typename T, int Q, bool INV, int LR>
+template <typename T, int Q, bool INV, int LR, int C>
 __device__ __forceinline__ void tile_subpass(cplx<T>* __restrict__ buf, int log2p2, const SmemTw<T>& tw, int log2M)
 {
     using V = cplx<T>;
     constexpr int LQ = ilog2c(Q);
+    constexpr int LC = ilog2c(C);
+    constexpr int S = C + 1;                     // row stride
     constexpr int R = 1 << LR;
     constexpr int nbq = R >> LQ;                 // butterflies per column
-    constexpr int NB = nbq * kTileCols;          // butterflies of the tile
+    constexpr int NB = nbq * C;                  // butterflies of the tile
     constexpr int BPT = (NB + 255) / 256;        // per thread
     const int p2 = 1 << log2p2;
     V u[BPT][Q];
@@ -170,9 +177,9 @@ __device__ __forceinline__ void tile_subpass(cplx<T>* __restrict__ buf, int log2
     for (int bi = 0; bi < BPT; ++bi) {
         const int b = threadIdx.x + bi * 256;
         if (NB % 256 == 0 || b < NB) {
-            const int j = b & (kTileCols - 1), i2 = b >> 4;
+            const int j = b & (C - 1), i2 = b >> LC;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) u[bi][q] = buf[(i2 + q * nbq) * kTileStride + j];
+            for (int q = 0; q < Q; ++q) u[bi][q] = buf[(i2 + q * nbq) * S + j];
         }
     }
     __syncthreads();
@@ -180,7 +187,7 @@ __device__ __forceinline__ void tile_subpass(cplx<T>* __restrict__ buf, int log2
     for (int bi = 0; bi < BPT; ++bi) {
         const int b = threadIdx.x + bi * 256;
         if (NB % 256 == 0 || b < NB) {
-            const int j = b & (kTileCols - 1), i2 = b >> 4;
+            const int j = b & (C - 1), i2 = b >> LC;
             const int k2 = i2 & (p2 - 1);
             if (p2 > 1) {
                 // W_{Q p2}^{q k2} = W_M^{q k2 M/(Q p2)}
@@ -195,39 +202,43 @@ __device__ __forceinline__ void tile_subpass(cplx<T>* __restrict__ buf, int log2
             dft_regs<T, Q, INV>(u[bi]);
             const int jo = ((i2 - k2) << LQ) + k2;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) buf[(jo + q * p2) * kTileStride + j] = u[bi][q];
+            for (int q = 0; q < Q; ++q) buf[(jo + q * p2) * S + j] = u[bi][q];
         }
     }
 }
 
-// All radix-2^LR sub-passes of one tile, in place in `buf`: a radix-2/4/8
-// sub-pass for LR mod 4, then radix-16 ones.  Ends with a block barrier.
-template <typename T, bool INV, int LR>
+// All radix-2^LR sub-passes of one tile of C columns, in place in `buf`: a
+// radix-2/4/8 sub-pass for LR mod 4, then radix-16 ones.  Ends with a block
+// barrier.
+template <typename T, bool INV, int LR, int C>
 __device__ __forceinline__ void tile_dft(cplx<T>* __restrict__ buf, const SmemTw<T>& tw, int log2M)
 {
     constexpr int rem = LR & 3;
     int log2p2 = 0;
     if (rem) {
-        tile_subpass<T, (1 << (rem ? rem : 1)), INV, LR>(buf, 0, tw, log2M);
+        tile_subpass<T, (1 << (rem ? rem : 1)), INV, LR, C>(buf, 0, tw, log2M);
         __syncthreads();
         log2p2 = rem;
     }
     for (; log2p2 < LR; log2p2 += 4) {
-        tile_subpass<T, 16, INV, LR>(buf, log2p2, tw, log2M);
+        tile_subpass<T, 16, INV, LR, C>(buf, log2p2, tw, log2M);
         __syncthreads();
     }
 }
 
 template <typename T, int LR, bool INV>
-__global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft_tile(const PassArgs a)
 {
     using V = cplx<T>;
     constexpr int R = 1 << LR;
+    constexpr int C = tile_cols(LR, (int)sizeof(V));
+    constexpr int LC = ilog2c(C);
+    constexpr int S = C + 1;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     V* b0 = (V*)tile_smem;
-    V* twm = b0 + R * kTileStride;
+    V* twm = b0 + R * S;
     const uint32_t log2nb = a.log2M - LR;
-    const int tpc = 1 << (log2nb - 4);       // tiles per curve (nb >= 16)
+    const int tpc = 1 << (log2nb - LC);      // tiles per curve (nb >= C)
     const int ci = blockIdx.x / tpc;
     const int ti = blockIdx.x % tpc;
     const int c = a.cls_curves[ci];
@@ -238,19 +249,19 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
     const V* __restrict__ rt = (const V*)a.tw;
     const uint64_t nb = 1ull << log2nb;
     const uint64_t p = 1ull << a.log2p;
-    const uint64_t i0 = (uint64_t)ti * kTileCols;
-    constexpr int PER = R * kTileCols / 256;  // elements per thread
+    const uint64_t i0 = (uint64_t)ti * C;
+    constexpr int PER = R * C / 256;  // elements per thread
     V v[PER];
 #pragma unroll
     for (int e = 0; e < PER; ++e) {  // every load in flight before any use
         const int idx = threadIdx.x + e * 256;
-        v[e] = src[i0 + (idx & (kTileCols - 1)) + (uint64_t)(idx >> 4) * nb];
+        v[e] = src[i0 + (idx & (C - 1)) + (uint64_t)(idx >> LC) * nb];
     }
     const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M);
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
         const int idx = threadIdx.x + e * 256;
-        const int r = idx >> 4, j = idx & (kTileCols - 1);
+        const int r = idx >> LC, j = idx & (C - 1);
         V x = v[e];
         if (p > 1) {
             const uint64_t k = (i0 + j) & (p - 1);
@@ -258,21 +269,21 @@ __global__ void __launch_bounds__(256) k_fft_tile(const PassArgs a)
             if (INV) w.y = -w.y;
             x = cmul(x, w);
         }
-        b0[r * kTileStride + j] = x;
+        b0[r * S + j] = x;
     }
     __syncthreads();
-    tile_dft<T, INV, LR>(b0, tw, (int)a.log2M);
+    tile_dft<T, INV, LR, C>(b0, tw, (int)a.log2M);
     const V* in = b0;
-    if (p >= (uint64_t)kTileCols) {
-        for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
-            const int q = idx >> 4, j = idx & (kTileCols - 1);
+    if (p >= (uint64_t)C) {
+        for (int idx = threadIdx.x; idx < R * C; idx += 256) {
+            const int q = idx >> LC, j = idx & (C - 1);
             const uint64_t i = i0 + j, k = i & (p - 1);
-            dst[((i - k) << LR) + k + (uint64_t)q * p] = in[q * kTileStride + j];
+            dst[((i - k) << LR) + k + (uint64_t)q * p] = in[q * S + j];
         }
-    } else {  // p == 1: column i owns y[i R .. i R + R)
-        for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
+    } else {  // p == 1 (the host guarantees p == 1 or p >= C): column i owns y[i R .. i R + R)
+        for (int idx = threadIdx.x; idx < R * C; idx += 256) {
             const int j = idx >> LR, q = idx & (R - 1);
-            dst[((i0 + j) << LR) + q] = in[q * kTileStride + j];
+            dst[((i0 + j) << LR) + q] = in[q * S + j];
         }
     }
 }
@@ -439,21 +450,26 @@ __device__ __forceinline__ void spectral_pair_tk(cplx<T>& za, cplx<T>& zb, uint6
 // passes in the reverse radix order).  Both passes touch column i through the
 // elements i + q p (q < R), and the conjugate partner M - t of t = i + q p is
 // in column p - i at row R-1-q; in column 0 itself at row R-q; and, for
-// i = p/2, in the same column at row R-1-q.  A block takes 8 columns and
-// their 8 partner columns -- column pairs (0, p/2), then (g, p - g) -- so all
-// three steps stay in shared memory, saving two passes over the spectrum and
-// the spectral kernel.  Output: y[i R + q] for the block's columns i.
+// i = p/2, in the same column at row R-1-q.  A block takes H = C/2 columns
+// and their H partner columns -- column pairs (0, p/2), then (g, p - g) -- so
+// all three steps stay in shared memory, saving two passes over the spectrum
+// and the spectral kernel.  Output: y[i R + q] for the block's columns i.
 template <typename T, int LR>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft_spectral(const PassArgs a, const void* __restrict__ A_all)
 {
     using V = cplx<T>;
     constexpr int R = 1 << LR;
+    constexpr int C = tile_cols(LR, (int)sizeof(V));
+    constexpr int LC = ilog2c(C);
+    constexpr int S = C + 1;
+    constexpr int H = C / 2;
+    constexpr int LH = LC - 1;
     extern __shared__ __align__(16) unsigned char tile_smem[];
     V* b0 = (V*)tile_smem;
-    V* twm = b0 + R * kTileStride;
+    V* twm = b0 + R * S;
     const uint32_t log2p = a.log2M - LR;
     const uint64_t p = 1ull << log2p;
-    const int tpc = (int)(p >> 4);
+    const int tpc = (int)(p >> LC);
     const int ci = blockIdx.x / tpc;
     const int ti = blockIdx.x % tpc;
     const int c = a.cls_curves[ci];
@@ -465,33 +481,33 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     const T* __restrict__ A = (const T*)A_all + cv.offh;
     const V* __restrict__ rt = (const V*)a.tw;
     const uint64_t M = 1ull << a.log2M;
-    // slot j < 8: column g = 8 ti + j; slot j + 8: its partner (p/2 for g = 0)
+    // slot j < H: column g = H ti + j; slot j + H: its partner (p/2 for g = 0)
     auto column = [&](int j) -> uint64_t {
-        const uint64_t g = (uint64_t)ti * 8 + (uint64_t)(j & 7);
-        if (j < 8) return g;
+        const uint64_t g = (uint64_t)ti * H + (uint64_t)(j & (H - 1));
+        if (j < H) return g;
         return g == 0 ? p / 2 : p - g;
     };
-    constexpr int PER = R * kTileCols / 256;  // elements per thread
+    constexpr int PER = R * C / 256;  // elements per thread
     V v[PER];
 #pragma unroll
     for (int e = 0; e < PER; ++e) {  // every load in flight before any use
         const int idx = threadIdx.x + e * 256;
-        v[e] = src[column(idx & (kTileCols - 1)) + (uint64_t)(idx >> 4) * p];
+        v[e] = src[column(idx & (C - 1)) + (uint64_t)(idx >> LC) * p];
     }
     const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M);
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
         const int idx = threadIdx.x + e * 256;
-        const int r = idx >> 4, j = idx & (kTileCols - 1);
+        const int r = idx >> LC, j = idx & (C - 1);
         // forward last pass: W_{R p}^{r k} = W_M^{r i} (k = i < p)
-        b0[r * kTileStride + j] = cmul(v[e], tw((uint64_t)r * column(j)));
+        b0[r * S + j] = cmul(v[e], tw((uint64_t)r * column(j)));
     }
     __syncthreads();
-    tile_dft<T, false, LR>(b0, tw, (int)a.log2M);
+    tile_dft<T, false, LR, C>(b0, tw, (int)a.log2M);
     V* in = b0;
     // spectral step on the conjugate pairs, in place: in[q][j] = Z_{column(j) + q p}
-    for (int idx = threadIdx.x; idx < R * 8; idx += 256) {
-        const int q = idx >> 3, j = idx & 7;
+    for (int idx = threadIdx.x; idx < R * H; idx += 256) {
+        const int q = idx >> LH, j = idx & (H - 1);
         const uint64_t col = column(j);
         const uint64_t t = col + (uint64_t)q * p;
         if (col == 0) {
@@ -503,26 +519,25 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
                 V o; o.x = Y0 + YM; o.y = Y0 - YM;
                 in[0] = o;
             } else if (q == R / 2) {  // k = M/2 pairs with itself: X = conj(Z), packed 2 conj(Y)
-                const V Yh = keep_phase(cconj(in[q * kTileStride]), A[M >> 1]);
+                const V Yh = keep_phase(cconj(in[q * S]), A[M >> 1]);
                 V oh; oh.x = (T)2 * Yh.x; oh.y = -(T)2 * Yh.y;
-                in[q * kTileStride] = oh;
+                in[q * S] = oh;
             } else if (q < R / 2) {
-                spectral_pair_tk<T>(in[q * kTileStride], in[(R - q) * kTileStride], t, M, rt, A);
+                spectral_pair_tk<T>(in[q * S], in[(R - q) * S], t, M, rt, A);
             }
         } else {
-            spectral_pair_tk<T>(in[q * kTileStride + j], in[(R - 1 - q) * kTileStride + j + 8], t, M, rt, A);
+            spectral_pair_tk<T>(in[q * S + j], in[(R - 1 - q) * S + j + H], t, M, rt, A);
         }
         if (ti == 0 && j == 0 && q < R / 2) {  // column p/2 pairs with itself
-            spectral_pair_tk<T>(in[q * kTileStride + 8], in[(R - 1 - q) * kTileStride + 8], p / 2 + (uint64_t)q * p,
-                                M, rt, A);
+            spectral_pair_tk<T>(in[q * S + H], in[(R - 1 - q) * S + H], p / 2 + (uint64_t)q * p, M, rt, A);
         }
     }
     __syncthreads();
     // inverse first pass (span 1: no input twiddle)
-    tile_dft<T, true, LR>(b0, tw, (int)a.log2M);
-    for (int idx = threadIdx.x; idx < R * kTileCols; idx += 256) {
+    tile_dft<T, true, LR, C>(b0, tw, (int)a.log2M);
+    for (int idx = threadIdx.x; idx < R * C; idx += 256) {
         const int j = idx >> LR, q = idx & (R - 1);
-        dst[(column(j) << LR) + q] = in[q * kTileStride + j];
+        dst[(column(j) << LR) + q] = in[q * S + j];
     }
 }
 
@@ -577,10 +592,18 @@ std::vector<int> tile_radices(uint32_t log2m, bool fp64)
     return r;
 }
 
+// Blocks of one tile pass (or of the fused spectral kernel) over a class:
+// curves x (M/R columns) / C columns per block.
+template <typename T>
+static int tile_blocks(int ncurves, uint32_t log2M, int LR)
+{
+    return ncurves << (log2M - LR - ilog2c(tile_cols(LR, (int)sizeof(cplx<T>))));
+}
+
 template <typename T, int LR, bool INV>
 static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
 {
-    const size_t smem = (((size_t)1 << LR) * kTileStride + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
+    const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
     cudaFuncSetAttribute(k_fft_tile<T, LR, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fft_tile<T, LR, INV><<<blocks, 256, smem, st>>>(a);
 }
@@ -621,7 +644,7 @@ void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void
             a.in = cur;
             a.out = (q + 1 == lr.size() && final_out) ? final_out : nxt;
             a.log2p = log2p;
-            const int blocks = k.ncurves << (a.log2M - lr[q] - 4);
+            const int blocks = tile_blocks<T>(k.ncurves, a.log2M, lr[q]);
             if (inverse) launch_tile<T, true>(lr[q], a, blocks, st);
             else launch_tile<T, false>(lr[q], a, blocks, st);
             if (launches) ++*launches;
@@ -706,7 +729,7 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
     uint32_t log2p = 0;
     for (int q = 0; q + 1 < P; ++q) {
         a.in = cur; a.out = nxt; a.log2p = log2p;
-        launch_tile<T, false>(lr[q], a, k.ncurves << (a.log2M - lr[q] - 4), st);
+        launch_tile<T, false>(lr[q], a, tile_blocks<T>(k.ncurves, a.log2M, lr[q]), st);
         if (launches) ++*launches;
         log2p += (uint32_t)lr[q];
         step();
@@ -714,8 +737,8 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
     const int LR = lr[P - 1];
     a.in = cur; a.out = nxt; a.log2p = log2p;
     {
-        const int blocks = k.ncurves << (a.log2M - LR - 4);
-        const size_t smem = (((size_t)1 << LR) * kTileStride + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
+        const int blocks = tile_blocks<T>(k.ncurves, a.log2M, LR);
+        const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
         switch (LR) {
 #define LC_FUSED_CASE(L)                                                                                   \
     case L:                                                                                                \
@@ -742,7 +765,7 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
     log2p = (uint32_t)LR;
     for (int q = P - 2; q >= 0; --q) {
         a.in = cur; a.out = nxt; a.log2p = log2p;
-        launch_tile<T, true>(lr[q], a, k.ncurves << (a.log2M - lr[q] - 4), st);
+        launch_tile<T, true>(lr[q], a, tile_blocks<T>(k.ncurves, a.log2M, lr[q]), st);
         if (launches) ++*launches;
         log2p += (uint32_t)lr[q];
         step();
