@@ -227,20 +227,25 @@ constexpr int kSlots = kSortTile / kSortThreads;  // elements per thread of a fu
 // the curve is gb[d] + (count of d in earlier warps) + (rank in its warp), and
 // the element writes x[position] = s[rank] straight from registers (the
 // stores are scattered anyway), with no shared-memory placement.
-// FULL: a tile of kSortTile elements (no bounds tests).  Expects wcnt zeroed
-// and gb set (after a block barrier).  Ends with a block barrier.
-template <typename T, bool FIRST, int MODE, bool FULL>
-__device__ __forceinline__ void sort_tile(const SortArgs& a, const void* kin, const uint32_t* vin, void* kout,
-                                          uint32_t* vout, int shift, uint64_t off, uint32_t e0, int tl,
-                                          typename key_of<T>::type* sk, uint32_t* sv,
-                                          uint32_t (*wcnt)[256], uint32_t* ldstart, uint32_t* gb,
-                                          uint32_t* wsum)
+// src_t / src_k / src_v point at the tile's first value / key / position
+// (global or shared memory).  FULL: a tile of kSortTile elements (no bounds
+// tests).  `hook` runs after the first block barrier that follows the reads
+// of the tile's input.  Expects wcnt zeroed and gb set (after a block
+// barrier).  Ends with a block barrier.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <typename T, bool FIRST, int MODE, bool FULL, typename Hook = NoHook>
+__device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict__ src_t,
+                                          const typename key_of<T>::type* __restrict__ src_k,
+                                          const uint32_t* __restrict__ src_v, void* kout, uint32_t* vout, int shift,
+                                          uint64_t off, uint32_t e0, int tl, typename key_of<T>::type* sk,
+                                          uint32_t* sv, uint32_t (*wcnt)[256], uint32_t* ldstart, uint32_t* gb,
+                                          uint32_t* wsum, Hook hook = Hook())
 {
     using K = typename key_of<T>::type;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const T* __restrict__ src_t = (const T*)a.src + off + e0;
-    const K* __restrict__ src_k = (const K*)kin + off + e0;
-    const uint32_t* __restrict__ src_v = vin + off + e0;
     if (FULL) tl = kSortTile;
     const int EW = (tl + kSortWarps - 1) / kSortWarps;  // elements per warp
     const uint32_t lt = (1u << lane) - 1u;
@@ -283,6 +288,7 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const void* kin, co
         rk[e] = valid ? base + below : 0xffffffffu;
     }
     __syncthreads();
+    hook();  // the tile's input has been read by every thread
     // per-digit prefix over warps (in place)
     uint32_t tot = 0;
 #pragma unroll
@@ -373,14 +379,17 @@ __global__ void __launch_bounds__(kSortThreads, 5) k_sort_scatter(const SortArgs
     gb[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
               a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
     __syncthreads();
+    const uint64_t off = a.curves[c].off;
+    const uint32_t e0 = (uint32_t)t * (uint32_t)a.tile_len;
+    const T* src_t = (const T*)a.src + off + e0;
+    const K* src_k = (const K*)a.keys_in + off + e0;
+    const uint32_t* src_v = a.vals_in + off + e0;
     if (a.tile_len == kSortTile)
-        sort_tile<T, FIRST, MODE, true>(a, a.keys_in, a.vals_in, a.keys_out, a.vals_out, a.shift,
-                                            a.curves[c].off, (uint32_t)t * (uint32_t)a.tile_len, a.tile_len, sk, sv,
-                                            wcnt, ldstart, gb, wsum);
+        sort_tile<T, FIRST, MODE, true>(a, src_t, src_k, src_v, a.keys_out, a.vals_out, a.shift, off, e0,
+                                        a.tile_len, sk, sv, wcnt, ldstart, gb, wsum);
     else
-        sort_tile<T, FIRST, MODE, false>(a, a.keys_in, a.vals_in, a.keys_out, a.vals_out, a.shift,
-                                             a.curves[c].off, (uint32_t)t * (uint32_t)a.tile_len, a.tile_len, sk, sv,
-                                             wcnt, ldstart, gb, wsum);
+        sort_tile<T, FIRST, MODE, false>(a, src_t, src_k, src_v, a.keys_out, a.vals_out, a.shift, off, e0,
+                                         a.tile_len, sk, sv, wcnt, ldstart, gb, wsum);
 }
 
 // Eq. 4 (Sec. 3.2.2) from the two iterates, both in natural order: one tile
