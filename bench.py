@@ -41,7 +41,7 @@ ALG_BYTES_PER_SAMPLE_ITER = 14  # read x 4 + read A 2 + read s 4 + write x 4 (FP
 SORT_BYTES_PER_ELEMENT = {4: 12 + 16 + 16 + 16, 8: 20 + 6 * 24 + 28}
 # DRAM bytes (read + write) of the four FP32 scatter passes per element, from
 # one ncu capture of the current kernel (profiles/sort_scatter_uniform_512x2^16.md)
-SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 = 1.891e9 / 2 ** 25
+SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 = 1.8893e9 / 2 ** 25
 WORKLOAD = (f"uniform batch: {NCURVES} curves x 2^{LOG2N} samples, dt=1 d, bending PL PSD "
             f"(f_br=1/300 d^-1, slopes 1 and 2), broken-PL ERDF [-4,0] break -1.5 slopes +0.4/-2.5, "
             f"{ITERS} E13 iterations, FP32")
