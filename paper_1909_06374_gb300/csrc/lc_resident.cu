@@ -653,15 +653,17 @@ void launch_cluster(const ResArgs& a, int ncurves, size_t smem, int smax, cudaSt
 
 }  // namespace
 
-// Path table (measured on GB300, 2^28 samples x 200 iterations per length):
-// the fused kernels win from 2^10 to 2^15 (2.6x at 2^10, 1.8x at 2^14, 1.07x
-// at 2^15), the multi-kernel path at 2^16 (1.33x); LC_PATH=resident also
-// uses the 4-CTA cluster kernel at 2^16.
+// Path table (measured on GB300, 2^28 samples x 200 iterations per length,
+// sample*iter/s): the one-CTA fused kernel wins from 2^10 to 2^14 (2^12:
+// 3.46e10 vs 2.39e10 multi-kernel, 2^13: 3.81e10 vs 2.81e10, 2^14: 3.60e10
+// vs 2.86e10), the multi-kernel path from 2^15 on (2^15: 2.90e10 vs 2.08e10
+// for the 2-CTA cluster kernel; 2^16: 2.90e10, the 4-CTA cluster kernel far
+// behind).  LC_PATH=resident also runs the cluster kernels at 2^15 and 2^16.
 bool resident_supported(const Plan& p, uint32_t log2n)
 {
     if (p.prec != LC_FP32 || log2n < kResMinLog2) return false;
     if (p.path_mode == 2) return false;
-    return log2n <= (p.path_mode == 1 ? kResClusterMaxLog2 : kResClusterMaxLog2 - 1);
+    return log2n <= (p.path_mode == 1 ? kResClusterMaxLog2 : kResMaxLog2);
 }
 
 size_t resident_exchange_floats(uint32_t log2n)

@@ -38,7 +38,7 @@ CASES = {
     "auto_fp32": ([8, 10, 12, 14, 15, 16, 17], LC_FP32, None),
     "auto_fp64": ([9, 12, 15], LC_FP64, None),
     "forced_multi": ([12, 14], LC_FP32, "multi"),
-    "forced_resident": ([16, 13], LC_FP32, "resident"),
+    "forced_resident": ([16, 15, 13], LC_FP32, "resident"),
 }
 
 

@@ -295,13 +295,13 @@ def test_long_full_size_sampled():
             assert np.array_equal(np.sort(seg), np.sort(d)), c
 
 
-@pytest.mark.parametrize("path", ["resident", "multi"])
-def test_forced_paths_one_step_at_2_16(path, monkeypatch):
-    """The per-length table picks one iteration path; both complete paths stay
-    correct: LC_PATH=resident runs 2^16 curves on the 4-CTA cluster kernel,
-    LC_PATH=multi runs 2^12 curves on the multi-kernel path."""
+@pytest.mark.parametrize("path,log2n", [("resident", 16), ("resident", 15), ("multi", 12)])
+def test_forced_paths_one_step(path, log2n, monkeypatch):
+    """The per-length table picks one iteration path; every complete path stays
+    correct: LC_PATH=resident runs 2^16 curves on the 4-CTA and 2^15 curves on
+    the 2-CTA cluster kernel, LC_PATH=multi runs 2^12 curves on the
+    multi-kernel path."""
     monkeypatch.setenv("LC_PATH", path)
-    log2n = 16 if path == "resident" else 12
     jobs = workloads.uniform(ncurves=3, log2n=log2n, iters=2)
     states, expect = [], []
     for j in jobs:
