@@ -34,8 +34,9 @@ struct SmemTw {
     const cplx<T>* t0;
     const cplx<T>* t1;
     const cplx<T>* t2;
+    const cplx<T>* tR;  // W_R^e, e < R: every twiddle of a radix-R pass's sub-passes
     bool three;
-    __device__ __forceinline__ cplx<T> operator()(uint64_t e) const
+    __device__ __forceinline__ cplx<T> operator()(uint32_t e) const
     {
         cplx<T> w = cmul(t1[(e >> 9) & (kTwLevel - 1)], t0[e & (kTwLevel - 1)]);
         if (three) w = cmul(t2[e >> 18], w);
@@ -43,16 +44,18 @@ struct SmemTw {
     }
 };
 
-__host__ __device__ constexpr int smem_tw_entries(int log2M)
+__host__ __device__ constexpr int smem_tw_entries(int log2M, int LR)
 {
-    return kTwLevel + (log2M >= 18 ? kTwLevel : (1 << (log2M - 9))) + (log2M > 18 ? (1 << (log2M - 18)) : 0);
+    return kTwLevel + (log2M >= 18 ? kTwLevel : (1 << (log2M - 9))) + (log2M > 18 ? (1 << (log2M - 18)) : 0) +
+           (1 << LR);
 }
 
-// Fills the tables at `mem` (smem_tw_entries(log2M) entries: 512, then the
-// 2^(log2M-9) or 512 of the second level, then those of the third) for a
-// length-M transform; ends with a block barrier.
+// Fills the tables at `mem` (smem_tw_entries(log2M, LR) entries: 512, then
+// the 2^(log2M-9) or 512 of the second level, then those of the third, then
+// W_R^e = W_M^{e M/R} for e < R = 2^LR, each read from the class table) for a
+// radix-R pass of a length-M transform; ends with a block barrier.
 template <typename T>
-__device__ __forceinline__ SmemTw<T> build_smem_tw(cplx<T>* mem, const cplx<T>* __restrict__ rt, int log2M)
+__device__ __forceinline__ SmemTw<T> build_smem_tw(cplx<T>* mem, const cplx<T>* __restrict__ rt, int log2M, int LR)
 {
     const uint64_t M = 1ull << log2M;
     SmemTw<T> tw;
@@ -60,13 +63,16 @@ __device__ __forceinline__ SmemTw<T> build_smem_tw(cplx<T>* mem, const cplx<T>* 
     tw.three = log2M > 18;
     const int n1 = log2M >= 18 ? kTwLevel : (1 << (log2M - 9));
     const int n2 = log2M > 18 ? (1 << (log2M - 18)) : 0;
+    const int lv = kTwLevel + n1 + n2;
     tw.t1 = mem + kTwLevel;
     tw.t2 = mem + kTwLevel + n1;
-    for (int x = threadIdx.x; x < kTwLevel + n1 + n2; x += blockDim.x) {
+    tw.tR = mem + lv;
+    for (int x = threadIdx.x; x < lv + (1 << LR); x += blockDim.x) {
         uint64_t e;
         if (x < kTwLevel) e = (uint64_t)x;
         else if (x < kTwLevel + n1) e = (uint64_t)(x - kTwLevel) << 9;
-        else e = (uint64_t)(x - kTwLevel - n1) << 18;
+        else if (x < lv) e = (uint64_t)(x - kTwLevel - n1) << 18;
+        else e = (uint64_t)(x - lv) << (log2M - LR);
         mem[x] = twiddle_M<T>(rt, e, M);
     }
     __syncthreads();
@@ -190,11 +196,11 @@ __device__ __forceinline__ void tile_subpass(cplx<T>* __restrict__ buf, int log2
             const int j = b & (C - 1), i2 = b >> LC;
             const int k2 = i2 & (p2 - 1);
             if (p2 > 1) {
-                // W_{Q p2}^{q k2} = W_M^{q k2 M/(Q p2)}
-                const uint64_t step = (uint64_t)k2 << (log2M - LQ - log2p2);
+                // W_{Q p2}^{q k2} = W_R^{q k2 R/(Q p2)}, q k2 < Q p2 <= R
+                const int sh = LR - LQ - log2p2;
 #pragma unroll
                 for (int q = 1; q < Q; ++q) {
-                    V w = tw((uint64_t)q * step);
+                    V w = tw.tR[(q * k2) << sh];
                     if (INV) w.y = -w.y;
                     u[bi][q] = cmul(u[bi][q], w);
                 }
@@ -247,25 +253,26 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     const V* __restrict__ src = (const V*)a.in + base;
     V* __restrict__ dst = (V*)a.out + base;
     const V* __restrict__ rt = (const V*)a.tw;
-    const uint64_t nb = 1ull << log2nb;
-    const uint64_t p = 1ull << a.log2p;
-    const uint64_t i0 = (uint64_t)ti * C;
+    // indices within a curve stay below M <= 2^26: 32-bit arithmetic
+    const uint32_t nb = 1u << log2nb;
+    const uint32_t p = 1u << a.log2p;
+    const uint32_t i0 = (uint32_t)ti * C;
     constexpr int PER = R * C / 256;  // elements per thread
     V v[PER];
 #pragma unroll
     for (int e = 0; e < PER; ++e) {  // every load in flight before any use
         const int idx = threadIdx.x + e * 256;
-        v[e] = src[i0 + (idx & (C - 1)) + (uint64_t)(idx >> LC) * nb];
+        v[e] = src[i0 + (uint32_t)(idx & (C - 1)) + (uint32_t)(idx >> LC) * nb];
     }
-    const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M);
+    const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M, LR);
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
         const int idx = threadIdx.x + e * 256;
         const int r = idx >> LC, j = idx & (C - 1);
         V x = v[e];
         if (p > 1) {
-            const uint64_t k = (i0 + j) & (p - 1);
-            V w = tw(((uint64_t)r * k) << (a.log2M - LR - a.log2p));
+            const uint32_t k = (i0 + (uint32_t)j) & (p - 1);
+            V w = tw(((uint32_t)r * k) << (a.log2M - LR - a.log2p));
             if (INV) w.y = -w.y;
             x = cmul(x, w);
         }
@@ -274,16 +281,16 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     __syncthreads();
     tile_dft<T, INV, LR, C>(b0, tw, (int)a.log2M);
     const V* in = b0;
-    if (p >= (uint64_t)C) {
+    if (p >= (uint32_t)C) {
         for (int idx = threadIdx.x; idx < R * C; idx += 256) {
             const int q = idx >> LC, j = idx & (C - 1);
-            const uint64_t i = i0 + j, k = i & (p - 1);
-            dst[((i - k) << LR) + k + (uint64_t)q * p] = in[q * S + j];
+            const uint32_t i = i0 + (uint32_t)j, k = i & (p - 1);
+            dst[((i - k) << LR) + k + (uint32_t)q * p] = in[q * S + j];
         }
     } else {  // p == 1 (the host guarantees p == 1 or p >= C): column i owns y[i R .. i R + R)
         for (int idx = threadIdx.x; idx < R * C; idx += 256) {
             const int j = idx >> LR, q = idx & (R - 1);
-            dst[((i0 + j) << LR) + q] = in[q * S + j];
+            dst[((i0 + (uint32_t)j) << LR) + (uint32_t)q] = in[q * S + j];
         }
     }
 }
@@ -425,12 +432,12 @@ __global__ void __launch_bounds__(256) k_spectral_tk(const SpecArgs a)
 // caller: za = Z_t, zb = Z_{M-t} in, Z'_t, Z'_{M-t} out.  The arithmetic runs
 // on the representative k = min(t, M - t), as in k_spectral_iter.
 template <typename T>
-__device__ __forceinline__ void spectral_pair_tk(cplx<T>& za, cplx<T>& zb, uint64_t t, uint64_t M,
+__device__ __forceinline__ void spectral_pair_tk(cplx<T>& za, cplx<T>& zb, uint32_t t, uint32_t M,
                                                  const cplx<T>* __restrict__ rt, const T* __restrict__ A)
 {
     using V = cplx<T>;
     const bool low = 2 * t < M;
-    const uint64_t k = low ? t : M - t;
+    const uint32_t k = low ? t : M - t;
     const V zk = low ? za : zb, zm = low ? zb : za;
     const V W = rt[k];
     V E; E.x = (T)0.5 * (zk.x + zm.x); E.y = (T)0.5 * (zk.y - zm.y);
@@ -468,7 +475,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     V* b0 = (V*)tile_smem;
     V* twm = b0 + R * S;
     const uint32_t log2p = a.log2M - LR;
-    const uint64_t p = 1ull << log2p;
+    const uint32_t p = 1u << log2p;  // indices within a curve: 32-bit (M <= 2^26)
     const int tpc = (int)(p >> LC);
     const int ci = blockIdx.x / tpc;
     const int ti = blockIdx.x % tpc;
@@ -480,10 +487,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     V* __restrict__ dst = (V*)a.out + base;
     const T* __restrict__ A = (const T*)A_all + cv.offh;
     const V* __restrict__ rt = (const V*)a.tw;
-    const uint64_t M = 1ull << a.log2M;
+    const uint32_t M = 1u << a.log2M;
     // slot j < H: column g = H ti + j; slot j + H: its partner (p/2 for g = 0)
-    auto column = [&](int j) -> uint64_t {
-        const uint64_t g = (uint64_t)ti * H + (uint64_t)(j & (H - 1));
+    auto column = [&](int j) -> uint32_t {
+        const uint32_t g = (uint32_t)ti * H + (uint32_t)(j & (H - 1));
         if (j < H) return g;
         return g == 0 ? p / 2 : p - g;
     };
@@ -492,15 +499,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
 #pragma unroll
     for (int e = 0; e < PER; ++e) {  // every load in flight before any use
         const int idx = threadIdx.x + e * 256;
-        v[e] = src[column(idx & (C - 1)) + (uint64_t)(idx >> LC) * p];
+        v[e] = src[column(idx & (C - 1)) + (uint32_t)(idx >> LC) * p];
     }
-    const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M);
+    const SmemTw<T> tw = build_smem_tw<T>(twm, rt, (int)a.log2M, LR);
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
         const int idx = threadIdx.x + e * 256;
         const int r = idx >> LC, j = idx & (C - 1);
         // forward last pass: W_{R p}^{r k} = W_M^{r i} (k = i < p)
-        b0[r * S + j] = cmul(v[e], tw((uint64_t)r * column(j)));
+        b0[r * S + j] = cmul(v[e], tw((uint32_t)r * column(j)));
     }
     __syncthreads();
     tile_dft<T, false, LR, C>(b0, tw, (int)a.log2M);
@@ -508,8 +515,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     // spectral step on the conjugate pairs, in place: in[q][j] = Z_{column(j) + q p}
     for (int idx = threadIdx.x; idx < R * H; idx += 256) {
         const int q = idx >> LH, j = idx & (H - 1);
-        const uint64_t col = column(j);
-        const uint64_t t = col + (uint64_t)q * p;
+        const uint32_t col = column(j);
+        const uint32_t t = col + (uint32_t)q * p;
         if (col == 0) {
             if (q == 0) {  // DC and Nyquist: Y_0 = A_0, Y_M = A_M sign(X_M), packed together
                 const V z0 = in[0];
@@ -529,7 +536,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
             spectral_pair_tk<T>(in[q * S + j], in[(R - 1 - q) * S + j + H], t, M, rt, A);
         }
         if (ti == 0 && j == 0 && q < R / 2) {  // column p/2 pairs with itself
-            spectral_pair_tk<T>(in[q * S + H], in[(R - 1 - q) * S + H], p / 2 + (uint64_t)q * p, M, rt, A);
+            spectral_pair_tk<T>(in[q * S + H], in[(R - 1 - q) * S + H], p / 2 + (uint32_t)q * p, M, rt, A);
         }
     }
     __syncthreads();
@@ -603,7 +610,7 @@ static int tile_blocks(int ncurves, uint32_t log2M, int LR)
 template <typename T, int LR, bool INV>
 static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
 {
-    const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
+    const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M, LR)) * sizeof(cplx<T>);
     cudaFuncSetAttribute(k_fft_tile<T, LR, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fft_tile<T, LR, INV><<<blocks, 256, smem, st>>>(a);
 }
@@ -738,7 +745,7 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
     a.in = cur; a.out = nxt; a.log2p = log2p;
     {
         const int blocks = tile_blocks<T>(k.ncurves, a.log2M, LR);
-        const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M)) * sizeof(cplx<T>);
+        const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M, LR)) * sizeof(cplx<T>);
         switch (LR) {
 #define LC_FUSED_CASE(L)                                                                                   \
     case L:                                                                                                \

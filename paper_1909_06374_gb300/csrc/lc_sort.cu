@@ -236,7 +236,7 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-template <typename T, bool FIRST, int MODE, bool FULL, typename Hook = NoHook>
+template <typename T, bool FIRST, int MODE, bool FULL, int THREADS = kSortThreads, typename Hook = NoHook>
 __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict__ src_t,
                                           const typename key_of<T>::type* __restrict__ src_k,
                                           const uint32_t* __restrict__ src_v, void* kout, uint32_t* vout, int shift,
@@ -245,21 +245,23 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
                                           uint32_t* wsum, Hook hook = Hook())
 {
     using K = typename key_of<T>::type;
+    constexpr int WARPS = THREADS / 32;
+    constexpr int SLOTS = kSortTile / THREADS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (FULL) tl = kSortTile;
-    const int EW = (tl + kSortWarps - 1) / kSortWarps;  // elements per warp
+    const int EW = (tl + WARPS - 1) / WARPS;  // elements per warp
     const uint32_t lt = (1u << lane) - 1u;
-    K key[kSlots];
-    uint32_t val[kSlots], rk[kSlots];
+    K key[SLOTS];
+    uint32_t val[SLOTS], rk[SLOTS];
     // ranking in two phases: every slot's load and peer mask first (independent
     // chains that overlap), then the short chain of per-warp digit counters;
     // every second slot takes its mask from the match instruction, the others
     // from eight ballots on the ALU pipe (measured on the 4096 x 2^16 batch:
     // match on none 6.04 ms of scatter per iteration, every 4th 5.62, every
     // 3rd 5.59, every 2nd 5.53)
-    uint32_t info[kSlots];  // digit | below << 8 | count << 16; 0xffffffff: empty slot
+    uint32_t info[SLOTS];  // digit | below << 8 | count << 16; 0xffffffff: empty slot
 #pragma unroll
-    for (int e = 0; e < kSlots; ++e) {
+    for (int e = 0; e < SLOTS; ++e) {
         const int j = e * 32 + lane;              // index within the warp's elements
         const int el = warp * EW + j;             // index within the tile
         const bool valid = FULL || (j < EW && el < tl);
@@ -277,7 +279,7 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
         info[e] = valid ? d | ((uint32_t)__popc(peers & lt) << 8) | ((uint32_t)__popc(peers) << 16) : 0xffffffffu;
     }
 #pragma unroll
-    for (int e = 0; e < kSlots; ++e) {
+    for (int e = 0; e < SLOTS; ++e) {
         const bool valid = info[e] != 0xffffffffu;
         const uint32_t d = info[e] & 255u, below = (info[e] >> 8) & 255u;
         uint32_t base = 0;
@@ -291,48 +293,52 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
     hook();  // the tile's input has been read by every thread
     // per-digit prefix over warps (in place)
     uint32_t tot = 0;
+    if (tid < 256) {
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t v = wcnt[w][tid];
-        wcnt[w][tid] = tot;
-        tot += v;
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t v = wcnt[w][tid];
+            wcnt[w][tid] = tot;
+            tot += v;
+        }
     }
     if (MODE == kSortArgsortScatter) {
         __syncthreads();
         // all loads of s before the thread's first store
         const T* __restrict__ s_in = (const T*)a.s_in + off;
         T* __restrict__ x_out = (T*)a.x_out + off;
-        T xn[kSlots];
+        T xn[SLOTS];
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
             if (rk[e] != 0xffffffffu) {
                 const uint32_t d = info[e] & 255u;
                 xn[e] = s_in[gb[d] + wcnt[warp][d] + rk[e]];
             }
         }
 #pragma unroll
-        for (int e = 0; e < kSlots; ++e)
+        for (int e = 0; e < SLOTS; ++e)
             if (rk[e] != 0xffffffffu) x_out[val[e]] = xn[e];
         __syncthreads();
         return;
     }
-    // the tile's digit starts
+    // the tile's digit starts (digits are threads 0..255)
     uint32_t incl = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    if (lane == 31) wsum[warp] = incl;
+    if (lane == 31 && tid < 256) wsum[warp] = incl;
     __syncthreads();
-    uint32_t woff = 0;
-    for (int q = 0; q < warp; ++q) woff += wsum[q];
-    const uint32_t ls = woff + incl - tot;
-    ldstart[tid] = ls;
-    gb[tid] -= ls;  // from here on: output index of tile position i of digit d = gb[d] + i
+    if (tid < 256) {
+        uint32_t woff = 0;
+        for (int q = 0; q < warp; ++q) woff += wsum[q];
+        const uint32_t ls = woff + incl - tot;
+        ldstart[tid] = ls;
+        gb[tid] -= ls;  // from here on: output index of tile position i of digit d = gb[d] + i
+    }
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < kSlots; ++e) {
+    for (int e = 0; e < SLOTS; ++e) {
         if (rk[e] != 0xffffffffu) {
             const uint32_t d = info[e] & 255u;
             const uint32_t lp = ldstart[d] + wcnt[warp][d] + rk[e];
@@ -344,7 +350,7 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
     K* __restrict__ kdst = (K*)kout + off;
     uint32_t* __restrict__ vdst = vout + off;
     T* __restrict__ sdst = (T*)a.s_out + off;
-    for (int i = tid; i < tl; i += kSortThreads) {
+    for (int i = tid; i < tl; i += THREADS) {
         const K k = sk[i];
         const uint32_t dest = gb[(uint32_t)(k >> shift) & 255u] + (uint32_t)i;
         if (MODE == 0) {
@@ -359,25 +365,27 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
 
 // One pass over one tile per block: the tile's output bases come from the
 // per-tile histograms and their two-level scan.
-template <typename T, bool FIRST, int MODE>
-__global__ void __launch_bounds__(kSortThreads, 5) k_sort_scatter(const SortArgs a)
+template <typename T, bool FIRST, int MODE, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_sort_scatter(const SortArgs a)
 {
+    static_assert(THREADS >= 256 && THREADS % 256 == 0, "the per-digit steps take one thread per digit");
     using K = typename key_of<T>::type;
+    constexpr int WARPS = THREADS / 32;
     const int ci = blockIdx.x / a.tpc;
     const int t = blockIdx.x % a.tpc;
     const int c = a.cls_curves[ci];
     if (!curve_active(a, c)) return;
     __shared__ K sk[kSortTile];
     __shared__ uint32_t sv[kSortTile];
-    __shared__ uint32_t wcnt[kSortWarps][256];
+    __shared__ uint32_t wcnt[WARPS][256];
     __shared__ uint32_t ldstart[256];
     __shared__ uint32_t gb[256];
     __shared__ uint32_t wsum[8];
     const int tid = threadIdx.x;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) wcnt[w][tid] = 0;
-    gb[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
-              a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
+    for (int q = tid; q < WARPS * 256; q += THREADS) (&wcnt[0][0])[q] = 0u;
+    if (tid < 256)
+        gb[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
+                  a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
     __syncthreads();
     const uint64_t off = a.curves[c].off;
     const uint32_t e0 = (uint32_t)t * (uint32_t)a.tile_len;
@@ -385,11 +393,11 @@ __global__ void __launch_bounds__(kSortThreads, 5) k_sort_scatter(const SortArgs
     const K* src_k = (const K*)a.keys_in + off + e0;
     const uint32_t* src_v = a.vals_in + off + e0;
     if (a.tile_len == kSortTile)
-        sort_tile<T, FIRST, MODE, true>(a, src_t, src_k, src_v, a.keys_out, a.vals_out, a.shift, off, e0,
-                                        a.tile_len, sk, sv, wcnt, ldstart, gb, wsum);
+        sort_tile<T, FIRST, MODE, true, THREADS>(a, src_t, src_k, src_v, a.keys_out, a.vals_out, a.shift, off, e0,
+                                                 a.tile_len, sk, sv, wcnt, ldstart, gb, wsum);
     else
-        sort_tile<T, FIRST, MODE, false>(a, src_t, src_k, src_v, a.keys_out, a.vals_out, a.shift, off, e0,
-                                         a.tile_len, sk, sv, wcnt, ldstart, gb, wsum);
+        sort_tile<T, FIRST, MODE, false, THREADS>(a, src_t, src_k, src_v, a.keys_out, a.vals_out, a.shift, off, e0,
+                                                  a.tile_len, sk, sv, wcnt, ldstart, gb, wsum);
 }
 
 // Eq. 4 (Sec. 3.2.2) from the two iterates, both in natural order: one tile
@@ -490,12 +498,21 @@ void launch_conv_reset(const Plan& p, cudaStream_t st)
     k_conv_reset<<<blocks, 256, 0, st>>>(p.conv.delta, n);
 }
 
+template <typename T, bool FIRST, int THREADS, int MINB>
+static void launch_scatter_v(int mode, const SortArgs& a, int blocks, cudaStream_t st)
+{
+    if (mode == 0) k_sort_scatter<T, FIRST, 0, THREADS, MINB><<<blocks, THREADS, 0, st>>>(a);
+    else if (mode == kSortArgsortScatter) k_sort_scatter<T, FIRST, kSortArgsortScatter, THREADS, MINB><<<blocks, THREADS, 0, st>>>(a);
+    else k_sort_scatter<T, FIRST, kSortKeysToValues, THREADS, MINB><<<blocks, THREADS, 0, st>>>(a);
+}
+
+// 256 threads and at most 48 registers (five blocks per SM): measured on the
+// 4096 x 2^16 batch, 5.60 ms of scatter per iteration against 6.18 ms with
+// 64 registers (four blocks) and 9.47 ms with 512-thread blocks.
 template <typename T, bool FIRST>
 static void launch_scatter(int mode, const SortArgs& a, int blocks, cudaStream_t st)
 {
-    if (mode == 0) k_sort_scatter<T, FIRST, 0><<<blocks, kSortThreads, 0, st>>>(a);
-    else if (mode == kSortArgsortScatter) k_sort_scatter<T, FIRST, kSortArgsortScatter><<<blocks, kSortThreads, 0, st>>>(a);
-    else k_sort_scatter<T, FIRST, kSortKeysToValues><<<blocks, kSortThreads, 0, st>>>(a);
+    launch_scatter_v<T, FIRST, 256, 5>(mode, a, blocks, st);
 }
 
 template <typename T, int TPB>

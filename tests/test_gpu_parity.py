@@ -261,8 +261,8 @@ def _one_step_in_batch(p, jobs, gpu_state, picks, prec=0):
 def test_ragged_full_size_sampled():
     """10000 curves, N log-uniform over 2^10..2^20, 100 iterations (the ragged
     workload as benchmarked): draw multisets of 40 sampled curves bit-exact, and
-    one iteration from the oracle's state per position on curves of every path
-    (single-CTA, 2- and 4-CTA cluster, multi-kernel)."""
+    one iteration from the oracle's state per position on curves of both paths
+    (the one-CTA fused kernel up to 2^14, the multi-kernel path above)."""
     jobs = workloads.ragged()
     rng = np.random.default_rng(1)
     sample = sorted(rng.choice(len(jobs), 40, replace=False).tolist())
@@ -293,6 +293,38 @@ def test_long_full_size_sampled():
             d = oracle.erdf_draws(oracle.job_params(j)[4:], 1 << j["log2n"], j["seed"], j["curve_id"], prec=0)
             seg = g[p.offsets[c]:p.offsets[c + 1]].cpu().numpy().astype(np.float64)
             assert np.array_equal(np.sort(seg), np.sort(d)), c
+
+
+def test_maximum_length_2_27():
+    """One curve of the largest length the boundary accepts (2^27 samples, three
+    tile passes per transform with three twiddle levels, 65536 sort tiles per
+    pass): 4096 sampled draws equal the oracle's Philox + inverse-CDF draw at
+    that index, bit for bit; the TK95 series has mean 0 and rms 1 (the
+    normalisation); after two iterations the series is a permutation of the
+    sorted draws, bit for bit (checked with torch's sort, not the library's)."""
+    n = 1 << 27
+    j = workloads.job(27, 2, seed=7, curve_id=3)
+    erdf = oracle.job_params(j)[4:]
+    rng = np.random.default_rng(5)
+    ks = np.unique(np.concatenate([[0, 1, n - 2, n - 1], rng.integers(0, n, 4092)]))
+    blocks = ks >> 1
+    ctr = np.stack([blocks & 0xffffffff, blocks >> 32, np.full_like(blocks, j["curve_id"]), np.ones_like(blocks)], 1)
+    key = np.tile(np.array([j["seed"] & 0xffffffff, j["seed"] >> 32], dtype=np.uint64), (len(ks), 1))
+    w = oracle.philox(ctr.astype(np.uint32), key.astype(np.uint32))
+    U = np.array([oracle.u01(int(r[2 * (k & 1)]), int(r[2 * (k & 1) + 1])) for r, k in zip(w, ks)])
+    want = oracle.erdf_icdf(erdf[:5], U).astype(np.float32)
+    with Plan([j], LC_FP32) as p:
+        tk = p.empty()
+        p.setup(out_tk=tk)
+        x0 = p.buffer(0)
+        s = p.buffer(2)
+        assert np.array_equal(x0[torch.as_tensor(ks, device=x0.device)].cpu().numpy(), want)
+        assert torch.equal(torch.sort(x0).values, s)
+        tkd = tk.double()
+        assert abs(float(tkd.mean())) < 1e-4 and abs(float(tkd.square().mean().sqrt()) - 1.0) < 1e-4
+        x2 = p.generate()
+        assert torch.equal(torch.sort(x2).values, s)
+        assert not torch.equal(x2, x0)
 
 
 @pytest.mark.parametrize("path,log2n", [("resident", 16), ("resident", 15), ("multi", 12)])
