@@ -227,22 +227,17 @@ constexpr int kSlots = kSortTile / kSortThreads;  // elements per thread of a fu
 // the curve is gb[d] + (count of d in earlier warps) + (rank in its warp), and
 // the element writes x[position] = s[rank] straight from registers (the
 // stores are scattered anyway), with no shared-memory placement.
-// src_t / src_k / src_v point at the tile's first value / key / position
-// (global or shared memory).  FULL: a tile of kSortTile elements (no bounds
-// tests).  `hook` runs after the first block barrier that follows the reads
-// of the tile's input.  Expects wcnt zeroed and gb set (after a block
-// barrier).  Ends with a block barrier.
-struct NoHook {
-    __device__ __forceinline__ void operator()() const {}
-};
-
-template <typename T, bool FIRST, int MODE, bool FULL, int THREADS = kSortThreads, typename Hook = NoHook>
+// src_t / src_k / src_v point at the tile's first value / key / position.
+// FULL: a tile of kSortTile elements (no bounds tests).  THREADS >= 256 (one
+// thread per digit in the per-digit steps).  Expects wcnt zeroed and gb set
+// (after a block barrier).  Ends with a block barrier.
+template <typename T, bool FIRST, int MODE, bool FULL, int THREADS = kSortThreads>
 __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict__ src_t,
                                           const typename key_of<T>::type* __restrict__ src_k,
                                           const uint32_t* __restrict__ src_v, void* kout, uint32_t* vout, int shift,
                                           uint64_t off, uint32_t e0, int tl, typename key_of<T>::type* sk,
                                           uint32_t* sv, uint32_t (*wcnt)[256], uint32_t* ldstart, uint32_t* gb,
-                                          uint32_t* wsum, Hook hook = Hook())
+                                          uint32_t* wsum)
 {
     using K = typename key_of<T>::type;
     constexpr int WARPS = THREADS / 32;
@@ -290,7 +285,6 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
         rk[e] = valid ? base + below : 0xffffffffu;
     }
     __syncthreads();
-    hook();  // the tile's input has been read by every thread
     // per-digit prefix over warps (in place)
     uint32_t tot = 0;
     if (tid < 256) {
@@ -364,7 +358,7 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
 }
 
 // One pass over one tile per block: the tile's output bases come from the
-// per-tile histograms and their two-level scan.
+// per-tile histograms and their scan.
 template <typename T, bool FIRST, int MODE, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_sort_scatter(const SortArgs a)
 {
