@@ -287,7 +287,7 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
     __syncthreads();
     // per-digit prefix over warps (in place)
     uint32_t tot = 0;
-    if (tid < 256) {
+    if (THREADS == 256 || tid < 256) {
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) {
             const uint32_t v = wcnt[w][tid];
@@ -321,9 +321,9 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    if (lane == 31 && tid < 256) wsum[warp] = incl;
+    if (lane == 31 && (THREADS == 256 || tid < 256)) wsum[warp] = incl;
     __syncthreads();
-    if (tid < 256) {
+    if (THREADS == 256 || tid < 256) {
         uint32_t woff = 0;
         for (int q = 0; q < warp; ++q) woff += wsum[q];
         const uint32_t ls = woff + incl - tot;
@@ -376,8 +376,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_sort_scatter(const SortArgs a
     __shared__ uint32_t gb[256];
     __shared__ uint32_t wsum[8];
     const int tid = threadIdx.x;
-    for (int q = tid; q < WARPS * 256; q += THREADS) (&wcnt[0][0])[q] = 0u;
-    if (tid < 256)
+#pragma unroll
+    for (int q = 0; q < WARPS * 256 / THREADS; ++q) (&wcnt[0][0])[q * THREADS + tid] = 0u;
+    if (THREADS == 256 || tid < 256)
         gb[tid] = a.hist[((size_t)ci * a.tpc + t) * 256 + tid] +
                   a.cbase[((size_t)ci * a.nchunks + t / kScanChunk) * 256 + tid];
     __syncthreads();
