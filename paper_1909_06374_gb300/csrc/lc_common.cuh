@@ -247,26 +247,48 @@ __device__ inline ErdfConst erdf_constants(const CurveDev& cv)
 }
 
 // Inverse CDF: v = U (M1+M2); below the break u = ub + ln(e1 + c1 v)/c1,
-// above u = ub + ln(1 + c2 (v - M1))/c2; lambda = e^{ln10 u} clamped.
+// above u = ub + ln(1 + c2 (v - M1))/c2 (spec_log1p's steps); lambda =
+// e^{ln10 u} clamped.  The two branches only prepare the argument of one
+// shared spec_log call (and the quotient log1p adds), so a warp whose lanes
+// fall on both sides of the break runs the logarithm once; every lane still
+// performs exactly the operations, in the order, of its own branch.
 __device__ __forceinline__ double erdf_draw(const ErdfConst& k, double U)
 {
     const double v = __dmul_rn(U, k.Msum);
-    double u;
+    double u = 0.0, arg = 1.0, add = 0.0, cdiv = 1.0, t = 0.0;
+    bool need_log = false, add_q = false, have_t = false;
     if (v < k.M1) {
         if (k.a1nz) {
-            const double t = spec_log(__dadd_rn(k.e1, __dmul_rn(k.c1, v)));
-            u = __dadd_rn(k.ub, __ddiv_rn(t, k.c1));
+            arg = __dadd_rn(k.e1, __dmul_rn(k.c1, v));
+            cdiv = k.c1;
+            need_log = true;
         } else {
             u = __dadd_rn(k.umin, v);
         }
     } else {
         if (k.a2nz) {
-            const double t = spec_log1p(__dmul_rn(k.c2, __dsub_rn(v, k.M1)));
-            u = __dadd_rn(k.ub, __ddiv_rn(t, k.c2));
+            const double y = __dmul_rn(k.c2, __dsub_rn(v, k.M1));
+            const double w = __dadd_rn(1.0, y);
+            cdiv = k.c2;
+            if (w == 1.0) {  // spec_log1p(y) = y
+                t = y;
+                have_t = true;
+            } else {
+                const double d = __dsub_rn(w, 1.0);
+                add = __ddiv_rn(__dsub_rn(y, d), w);
+                arg = w;
+                need_log = add_q = true;
+            }
         } else {
             u = __dadd_rn(k.ub, __dsub_rn(v, k.M1));
         }
     }
+    if (need_log) {
+        const double L = spec_log(arg);
+        t = add_q ? __dadd_rn(L, add) : L;
+        have_t = true;
+    }
+    if (have_t) u = __dadd_rn(k.ub, __ddiv_rn(t, cdiv));
     double lam = spec_exp(__dmul_rn(LC_LN10, u));
     if (lam < k.lo) lam = k.lo;
     if (lam > k.hi) lam = k.hi;

@@ -27,7 +27,11 @@ k_tk_spectrum(const CurveDev* __restrict__ curves, const int* __restrict__ cls_c
     const int jb = blockIdx.x % blocks_per_curve;
     const CurveDev cv = curves[cls_curves[ci]];
     const uint64_t nh = 1ull << (cv.log2n - 1);
-    const double nd = (double)(1ull << cv.log2n);
+    // y_j = f_j / f_br = j c; Eq. 3 as 1 / (e^{a_lo ln y} + e^{a_hi ln y}) (one
+    // logarithm for both terms); the amplitude sqrt(P/2) sqrt(-2 ln U1) as one
+    // square root: these are the FP64 operations this FP64-rate-bound kernel
+    // spends its time on
+    const double c = 1.0 / ((double)(1ull << cv.log2n) * cv.dt * cv.f_br);
     const bool fixed = cv.coeffs == 1;
     double acc = 0.0, acc_p = 0.0;
 #pragma unroll
@@ -38,19 +42,18 @@ k_tk_spectrum(const CurveDev* __restrict__ curves, const int* __restrict__ cls_c
         if (j > 0) {
             const uint4 w = philox(j, cv.curve_id, 0u, cv.seed);
             const double U1 = unit_open(w.x, w.y), U2 = unit_open(w.z, w.w);
-            const double rad = fixed ? 1.0 : sqrt(-2.0 * log(U1));
+            const double lu = fixed ? 0.0 : log(U1);  // rad^2 = -2 lu
             double sn, cs;
             sincospi(2.0 * U2, &sn, &cs);
-            const double f = (double)j / (nd * cv.dt);
-            const double y = f / cv.f_br;
-            const double P = 1.0 / (pow(y, cv.a_lo) + pow(y, cv.a_hi));
+            const double ly = log((double)j * c);
+            const double P = 1.0 / (exp(cv.a_lo * ly) + exp(cv.a_hi * ly));
             if (j < nh) {
-                const double a = fixed ? sqrt(P) : sqrt(P * 0.5);
-                X = make_double2(a * rad * cs, a * rad * sn);
+                const double a = fixed ? sqrt(P) : sqrt(-P * lu);
+                X = make_double2(a * cs, a * sn);
                 acc += 2.0 * (X.x * X.x + X.y * X.y);
                 acc_p += 2.0 * P;
             } else {
-                X = make_double2(fixed ? (cs < 0.0 ? -sqrt(P) : sqrt(P)) : sqrt(P) * rad * cs, 0.0);
+                X = make_double2(fixed ? (cs < 0.0 ? -sqrt(P) : sqrt(P)) : sqrt(-2.0 * P * lu) * cs, 0.0);
                 acc += X.x * X.x;
                 acc_p += P;
             }
@@ -93,30 +96,33 @@ __global__ void k_sigma(const int* __restrict__ cls_curves, int ncurves, int blo
 
 // Target amplitudes of the normalised TK95 series: A_j = |X_j| / sigma, A_0 = 0;
 // with PSD targets A_j = sqrt(P_j) / sigma_P.
+// One block covers kAmpTile bins of one curve (blockIdx.x = curve of the
+// class x chunks per curve + chunk), so no thread divides by N/2 + 1.
+constexpr int kAmpTile = 1024;
 template <typename T>
-__global__ void k_amplitudes(const CurveDev* __restrict__ curves, const int* __restrict__ cls_curves,
-                             int ncurves, uint32_t log2n, const double2* __restrict__ spec,
-                             const double* __restrict__ sigma, const double* __restrict__ sigma_p,
-                             T* __restrict__ A)
+__global__ void __launch_bounds__(256) k_amplitudes(const CurveDev* __restrict__ curves,
+                                                    const int* __restrict__ cls_curves, int chunks, uint32_t log2n,
+                                                    const double2* __restrict__ spec,
+                                                    const double* __restrict__ sigma,
+                                                    const double* __restrict__ sigma_p, T* __restrict__ A)
 {
     const uint64_t nh1 = (1ull << (log2n - 1)) + 1;
-    const uint64_t total = (uint64_t)ncurves * nh1;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const int ci = (int)(t / nh1);
-        const uint64_t j = t - (uint64_t)ci * nh1;
-        const int c = cls_curves[ci];
-        const CurveDev& cv = curves[c];
-        const uint64_t offh = cv.offh;
+    const int c = cls_curves[blockIdx.x / chunks];
+    const CurveDev& cv = curves[c];
+    const uint64_t j0 = (uint64_t)(blockIdx.x % chunks) * kAmpTile;
+    const bool psd = cv.targets == 1;
+    const double inv = 1.0 / (psd ? sigma_p[c] : sigma[c]);
+    const double cy = 1.0 / ((double)(1ull << log2n) * cv.dt * cv.f_br);
+    for (uint64_t j = j0 + threadIdx.x; j < j0 + kAmpTile && j < nh1; j += blockDim.x) {
         double a = 0.0;
-        if (j > 0 && cv.targets == 1) {
-            const double y = (double)j / ((double)(1ull << log2n) * cv.dt) / cv.f_br;
-            a = sqrt(1.0 / (pow(y, cv.a_lo) + pow(y, cv.a_hi))) / sigma_p[c];
+        if (j > 0 && psd) {
+            const double ly = log((double)j * cy);
+            a = sqrt(1.0 / (exp(cv.a_lo * ly) + exp(cv.a_hi * ly))) * inv;
         } else if (j > 0) {
-            const double2 X = spec[offh + j];
-            a = hypot(X.x, X.y) / sigma[c];
+            const double2 X = spec[cv.offh + j];
+            a = sqrt(X.x * X.x + X.y * X.y) * inv;
         }
-        A[offh + j] = (T)a;
+        A[cv.offh + j] = (T)a;
     }
 }
 
@@ -227,9 +233,10 @@ void launch_tk_spectrum(const Plan& p, const ClassInfo& k, cudaStream_t st)
 template <typename T>
 void launch_amplitudes(const Plan& p, const ClassInfo& k, cudaStream_t st)
 {
-    const uint64_t work = (uint64_t)k.ncurves * ((1ull << (k.log2n - 1)) + 1);
-    k_amplitudes<T><<<grid_for(work, 256), 256, 0, st>>>(p.d_curves, k.d_curves, k.ncurves, k.log2n,
-                                                         p.d_spec, p.d_sigma, p.d_sigma + p.ncurves, (T*)p.d_A);
+    const uint64_t nh1 = (1ull << (k.log2n - 1)) + 1;
+    const int chunks = (int)((nh1 + kAmpTile - 1) / kAmpTile);
+    k_amplitudes<T><<<k.ncurves * chunks, 256, 0, st>>>(p.d_curves, k.d_curves, chunks, k.log2n, p.d_spec,
+                                                        p.d_sigma, p.d_sigma + p.ncurves, (T*)p.d_A);
 }
 
 void launch_erdf_constants(const Plan& p, cudaStream_t st)
