@@ -104,6 +104,16 @@ int path_mode_from_env()
     return 0;
 }
 
+int resident_max_log2_from_env()
+{
+    const char* e = std::getenv("LC_RESIDENT_MAX_LOG2");
+    if (!e) return -1;
+    char* end = nullptr;
+    const long v = std::strtol(e, &end, 10);
+    if (end == e || *end != 0 || v < 9 || v > 16) return -1;
+    return (int)v;
+}
+
 template <typename T>
 static lc_status build_tables(Plan& p)
 {
@@ -131,11 +141,14 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->device = device;
     p->prec = prec;
     p->ncurves = njobs;
-    // Path selection (a tuning knob; results depend only on length and
-    // precision, never on the batch): LC_PATH=multi forces the multi-kernel
-    // iteration everywhere, LC_PATH=resident uses the fused kernels wherever
-    // they apply, the default follows the measured per-length table.
+    // Path selection (a tuning knob; results depend only on length,
+    // precision and the path, never on the batch): LC_PATH=multi forces the
+    // multi-kernel iteration everywhere, LC_PATH=resident uses the fused
+    // kernels wherever they apply, the default follows the per-length table
+    // measured by the autotuning sweep (autotune.py), whose crossover
+    // LC_RESIDENT_MAX_LOG2 overrides.
     p->path_mode = path_mode_from_env();
+    p->res_max_log2 = resident_max_log2_from_env();
     p->jobs.assign(jobs, jobs + njobs);
     const size_t ts = prec == LC_FP32 ? 4 : 8;
 

@@ -83,6 +83,7 @@ struct Plan {
     uint64_t last_launches = 0;
     bool setup_done = false;
     int path_mode = 0;        // 0 auto (measured table), 1 resident where possible, 2 multi-kernel
+    int res_max_log2 = -1;    // auto mode: longest length on the fused kernels (-1: the built-in table)
 
     // convergence test (Sec. 3.2.2, Eq. 4), off until lc_plan_set_convergence
     bool conv_on = false;
@@ -180,6 +181,9 @@ template <typename T> void launch_conv_delta(const Plan& p, const ClassInfo& k, 
 bool resident_supported(const Plan& p, uint32_t log2n);
 // path mode from the environment: LC_PATH=resident -> 1, multi -> 2, else 0 (auto)
 int path_mode_from_env();
+// LC_RESIDENT_MAX_LOG2 (9..16: the longest length the auto mode runs on the
+// fused kernels; 9 = none), else -1
+int resident_max_log2_from_env();
 // floats of cluster exchange area per curve of length 2^log2n (0: none needed)
 size_t resident_exchange_floats(uint32_t log2n);
 // Runs n_it iterations (from the plan's current iteration index) of every

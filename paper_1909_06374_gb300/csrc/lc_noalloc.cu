@@ -70,6 +70,7 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     p.prec = LC_FP32;
     p.ncurves = 1;
     p.path_mode = path_mode_from_env();
+    p.res_max_log2 = resident_max_log2_from_env();
     const size_t n = (size_t)1 << job->log2n, nh = n / 2 + 1, ts = 4;
     CurveDev cv = curve_from_job(*job);
     cv.off = 0; cv.offh = 0; cv.cls = 0; cv.tab = 0;

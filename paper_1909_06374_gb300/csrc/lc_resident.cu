@@ -658,12 +658,15 @@ void launch_cluster(const ResArgs& a, int ncurves, size_t smem, int smax, cudaSt
 // 3.46e10 vs 2.39e10 multi-kernel, 2^13: 3.81e10 vs 2.81e10, 2^14: 3.60e10
 // vs 2.86e10), the multi-kernel path from 2^15 on (2^15: 2.90e10 vs 2.08e10
 // for the 2-CTA cluster kernel; 2^16: 2.90e10, the 4-CTA cluster kernel far
-// behind).  LC_PATH=resident also runs the cluster kernels at 2^15 and 2^16.
+// behind).  LC_PATH=resident also runs the cluster kernels at 2^15 and 2^16;
+// LC_RESIDENT_MAX_LOG2 moves the crossover of the auto mode (autotune.py
+// measures it on the GPU at hand).
 bool resident_supported(const Plan& p, uint32_t log2n)
 {
     if (p.prec != LC_FP32 || log2n < kResMinLog2) return false;
     if (p.path_mode == 2) return false;
-    return log2n <= (p.path_mode == 1 ? kResClusterMaxLog2 : kResMaxLog2);
+    if (p.path_mode == 1) return log2n <= kResClusterMaxLog2;
+    return log2n <= (uint32_t)(p.res_max_log2 >= 0 ? p.res_max_log2 : (int)kResMaxLog2);
 }
 
 size_t resident_exchange_floats(uint32_t log2n)
