@@ -180,6 +180,13 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->total = off;
     p->total_h = offh;
 
+    for (auto& k : p->classes) {
+        if (k.log2n - 1 >= 12 && !tile_schedule_ok(k.log2n - 1, prec == LC_FP64)) {
+            set_error("internal: no tile schedule for log2n = " + std::to_string(k.log2n));
+            delete p;
+            return LC_ERR_INVALID;
+        }
+    }
     // arena layout
     size_t hist = 0, cbase = 0, partial = 0, twb = 0, rxb = 0;
     for (auto& k : p->classes) {

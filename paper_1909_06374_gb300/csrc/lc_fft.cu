@@ -607,6 +607,28 @@ static int tile_blocks(int ncurves, uint32_t log2M, int LR)
     return ncurves << (log2M - LR - ilog2c(tile_cols(LR, (int)sizeof(cplx<T>))));
 }
 
+// The tile kernels need nb = M/R >= C columns per curve, and a span p that
+// is 1 or at least C (their two output layouts); the fused spectral kernel
+// needs M/R >= C for the last forward radix.  Checked for the forward and
+// the (reversed) inverse radix order of a length-2^log2M tile-path transform.
+bool tile_schedule_ok(uint32_t log2M, bool fp64)
+{
+    const std::vector<int> lr = tile_radices(log2M, fp64);
+    const int eb = fp64 ? 16 : 8;
+    for (int dir = 0; dir < 2; ++dir) {
+        uint32_t log2p = 0;
+        for (size_t q = 0; q < lr.size(); ++q) {
+            const int L = dir == 0 ? lr[q] : lr[lr.size() - 1 - q];
+            const uint32_t C = (uint32_t)tile_cols(L, eb);
+            if ((1u << (log2M - L)) < C) return false;
+            if (log2p > 0 && (1u << log2p) < C) return false;
+            log2p += (uint32_t)L;
+        }
+    }
+    const int Ls = lr.back();
+    return (1u << (log2M - Ls)) >= (uint32_t)tile_cols(Ls, eb);
+}
+
 template <typename T, int LR, bool INV>
 static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
 {

@@ -142,6 +142,9 @@ template <typename T> void launch_erdf_draws(const Plan& p, const ClassInfo& k, 
 
 // FFT stage (lc_fft.cu)
 std::vector<int> fft_radices(uint32_t log2m);
+// Whether the tile-path passes of a length-2^log2M transform meet the tile
+// kernels' shape rules (host check at plan creation).
+bool tile_schedule_ok(uint32_t log2M, bool fp64);
 template <typename T> void launch_twiddles(const ClassInfo& k, cudaStream_t st);
 // Complex FFT of every curve of the class (forward: e^{-}, inverse: e^{+}),
 // ping-ponging between `in` and `other`; the last pass writes `final_out`
