@@ -47,6 +47,14 @@ JOBSETS = {
         workloads.job(17, 2, seed=25, curve_id=4, linear_space=1, **workloads.ERDF_SHAPES["lognormal"]),
         workloads.job(10, 3, seed=26, curve_id=5, linear_space=1, **workloads.ERDF_SHAPES["table2"]),
     ],
+    # zero ERDF slopes below / above the break (the linear pieces of the
+    # inverse CDF), directly and through linear_space (slope -1 + 1 = 0)
+    "zero_slopes": lambda: [
+        workloads.job(12, 3, seed=41, curve_id=0, slope_low=0.0),
+        workloads.job(11, 3, seed=42, curve_id=1, slope_high=0.0),
+        workloads.job(9, 3, seed=43, curve_id=2, slope_low=-1.0, linear_space=1),
+        workloads.job(13, 2, seed=44, curve_id=3, slope_low=0.0, slope_high=0.0),
+    ],
     # PSD variants: fixed-amplitude TK coefficients, PSD target amplitudes, a
     # single power law (equal slopes), on both iteration paths
     "psd_variants": lambda: [
