@@ -1,0 +1,101 @@
+"""Accuracy of the CUDA path against the FP64 oracle, stated per workload.
+
+For sampled curves of each of the five workloads (single FP64 curve, uniform
+batch, long curves, ragged batch, serving stream): the TK95-stage error
+(relative L2 of the normalised TK95 series against the oracle's), and for one
+iteration from the oracle's state the per-position comparison -- positions
+that differ, how many of them the near-tie rule exempts, the median and
+largest rank displacement and Spearman's rho between the two permutations.
+Curves enter a plan of their own: the results depend only on the length, the
+precision and the path, never on the rest of the batch (a property tested
+elsewhere).  Where one oracle iteration is too slow at the workload's length
+(2^26 samples, serving jobs above 2^20) the same parameters at a shorter
+length stand in, and the table says so.  Set LC_ACCURACY_REPORT to a file
+name to get the table as JSON."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_06374_gb300 import LC_FP32, LC_FP64, Plan, workloads
+from tests.parity import position_check, rank_stats, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    """(workload, precision, job used for the TK stage, job used for one iteration)."""
+    out = []
+    j = workloads.single()[0]
+    out.append(("single 1 x 2^14, FP64", LC_FP64, j, j))
+    uni = workloads.uniform()
+    for c in (0, 2047):
+        out.append((f"uniform 4096 x 2^16 (curve {c})", LC_FP32, uni[c], uni[c]))
+    lng = workloads.long_curves()
+    for c in (0, 5):
+        out.append((f"long 8 x 2^26 (curve {c}; iteration at 2^22)", LC_FP32, lng[c], dict(lng[c], log2n=22)))
+    rag = workloads.ragged()
+    first = {}
+    for c, jb in enumerate(rag):
+        first.setdefault(jb["log2n"], c)
+    for L in (10, 14, 17, 20):
+        c = first[L]
+        out.append((f"ragged (curve {c}, 2^{L})", LC_FP32, rag[c], rag[c]))
+    srv = [jb for _, jb in workloads.serving_stream(duration=1.0)]
+    by_len = sorted(srv, key=lambda q: q["log2n"])
+    for jb in (by_len[0], by_len[len(by_len) // 2], by_len[-1]):
+        it = jb if jb["log2n"] <= 20 else dict(jb, log2n=20)
+        tag = "" if jb["log2n"] <= 20 else "; iteration at 2^20"
+        out.append((f"serving (job {jb['curve_id']}, 2^{jb['log2n']}{tag})", LC_FP32, jb, it))
+    return out
+
+
+def _tk_error(job, prec):
+    par = oracle.job_params(job)
+    x_tk, _, _ = oracle.tk_series(job["log2n"], par[0], par[1:4], job["seed"], job["curve_id"],
+                                  coeffs=job.get("tk_coeffs", 0), targets=job.get("tk_targets", 0))
+    with Plan([job], prec) as p:
+        tk = p.empty()
+        p.setup(out_tk=tk)
+        tk = tk.cpu().numpy().astype(np.float64)
+    return rel_l2(tk, x_tk)
+
+
+def _one_iteration(job, prec):
+    po = 0 if prec == LC_FP32 else 1
+    r = oracle.generate(dict(job, iters=0), prec=po, want=("x", "A", "s"))
+    xk, _, _ = oracle.iterate(r["A"], r["s"], r["x"], 1)
+    x1, xa, _ = oracle.iterate(r["A"], r["s"], xk, 1, want_adj=True)
+    with Plan([job], prec) as p:
+        p.setup()
+        p.set_state(torch.tensor(xk, dtype=p.dtype, device="cuda"))
+        p.iterate(1)
+        got = p.get_state().cpu().numpy().astype(np.float64)
+    pc = position_check(got, x1, r["s"], xa)
+    rs = rank_stats(got, x1)
+    return pc, rs
+
+
+def test_accuracy_per_workload():
+    rows = []
+    for name, prec, jtk, jit in _cases():
+        err = _tk_error(jtk, prec)
+        pc, rs = _one_iteration(jit, prec)
+        rows.append(dict(workload=name, tk_rel_l2=err, n=pc["n"], mismatch=pc["mismatch"], exempt=pc["exempt"],
+                         fail=pc["fail"], median_disp=rs["median_disp"], max_disp=rs["max_disp"],
+                         spearman=rs["spearman"]))
+    print("\n| workload | TK95 rel. L2 | positions | differ | exempt (near ties) | rank disp. median / max | Spearman |")
+    print("|---|---|---|---|---|---|---|")
+    for r in rows:
+        print(f"| {r['workload']} | {r['tk_rel_l2']:.2e} | {r['n']} | {r['mismatch']} | {r['exempt']} | "
+              f"{r['median_disp']:.0f} / {r['max_disp']:.0f} | {r['spearman']:.9f} |")
+    out = os.environ.get("LC_ACCURACY_REPORT")
+    if out:
+        with open(out, "w") as f:
+            json.dump(rows, f, indent=1)
+    for r in rows:
+        assert r["tk_rel_l2"] <= (2e-5 if "FP64" not in r["workload"] else 1e-12), r
+        assert r["fail"] == 0, r
