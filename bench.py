@@ -156,16 +156,32 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ oracle
-def cpu_baseline_run(ncurves, iters, cores):
+def cpu_baseline_run(ncurves, iters, cores, jobs=None, prec=0):
     """The FP64 CPU oracle on `ncurves` curves of the workload (`iters`
-    iterations each), one curve per host thread; returns samples*iter/s."""
+    iterations each), or on the given jobs, one curve per host thread;
+    returns samples*iter/s, the threads used and the seconds."""
     import oracle
     oracle.build()
-    jobs = workloads.uniform(ncurves=ncurves, log2n=LOG2N, iters=iters)
+    if jobs is None:
+        jobs = workloads.uniform(ncurves=ncurves, log2n=LOG2N, iters=iters)
     t0 = time.perf_counter()
-    _, used = oracle.generate_batch(jobs, prec=0, nthreads=cores)
+    _, used = oracle.generate_batch(jobs, prec=prec, nthreads=cores)
     dt = time.perf_counter() - t0
-    return ncurves * (1 << LOG2N) * iters / dt, used, dt
+    return workloads.sample_iters(jobs) / dt, min(used, len(jobs)), dt  # threads that had a curve
+
+
+def cpu_baseline_sample(workload, cores):
+    """A bounded sample of a non-headline workload for the CPU oracle (a few to
+    some tens of seconds of CPU work) and its description."""
+    if workload == "single":
+        return workloads.single(), 1, "the whole workload: 1 curve x 2^14 samples x 100 iterations, FP64"
+    if workload == "long":
+        jobs = [dict(j, log2n=22, iters=2) for j in workloads.long_curves()][:cores]
+        return jobs, 0, (f"{len(jobs)} of the long curves' parameter sets at 2^22 samples (2^26 takes minutes "
+                         "per oracle iteration) x 2 iterations, one curve per thread")
+    jobs = [dict(j, iters=5) for j in workloads.ragged()[:cores]]
+    return jobs, 0, (f"the first {len(jobs)} ragged curves (their own lengths 2^10..2^20 and parameters) x 5 "
+                     "iterations, one curve per thread")
 
 
 def run_reference(args):
@@ -366,12 +382,16 @@ def run_gpu(args):
             "setup_ms": setup_ms}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and args.workload == "uniform":
+    if rank == 0 and not args.no_cpu_baseline and args.erdf is None and args.convergence is None:
         cores = os.cpu_count() or 1
-        v, used, dt = cpu_baseline_run(cores, ITERS, cores)
-        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
-               "sample": f"{cores} curves x 2^{LOG2N} samples x {ITERS} iterations (one curve per thread, "
-                         f"{dt:.1f} s)"}
+        if args.workload == "uniform":
+            v, used, dt = cpu_baseline_run(cores, ITERS, cores)
+            sample = f"{cores} curves x 2^{LOG2N} samples x {ITERS} iterations (one curve per thread, {dt:.1f} s)"
+        else:
+            cjobs, cprec, sample = cpu_baseline_sample(args.workload, cores)
+            v, used, dt = cpu_baseline_run(0, 0, cores, jobs=cjobs, prec=cprec)
+            sample += f" ({dt:.1f} s)"
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
