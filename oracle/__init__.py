@@ -40,11 +40,15 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The loaded oracle library.  ORACLE_LIB names another build of oracle.c
+    to load instead (the mutation test loads copies with a planted mistake)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB)
+            path = os.environ.get("ORACLE_LIB")
+            if not path:
+                path = build()
+            L = ctypes.CDLL(path)
             P = ctypes.c_void_p
             d, u32, u64, i32, sz = (ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64,
                                     ctypes.c_int, ctypes.c_size_t)
@@ -213,6 +217,12 @@ def tk_series(log2n, dt, psd_params, seed, curve_id, coeffs=0, targets=0):
 def argsort(v):
     v = _f64(v); perm = np.empty(v.size, dtype=np.int64)
     lib().or_argsort(v.size, _p(v), _p(perm)); return perm
+
+
+def sort(v):
+    """Ascending sort of a copy (the sort of the ERDF draws)."""
+    v = _f64(v).copy()
+    lib().or_sort(v.size, _p(v)); return v
 
 
 def iterate(A, s, x, iters, want_adj=False):

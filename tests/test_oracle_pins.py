@@ -185,6 +185,24 @@ def test_erdf_icdf_endpoints_and_break():
     assert np.all(np.diff(oracle.erdf_icdf(erdf, U)) >= 0)
 
 
+def test_erdf_draws_stay_in_the_support():
+    """Every draw lies in [lambda_min, lambda_max] (Eq. 1 is truncated to that
+    range), also at the extreme uniforms where the rounding of the inverse CDF
+    would otherwise step a few ulp outside; the endpoints are taken as
+    e^{ln10 log lambda}, the oracle's exp being pinned to libm above.  The
+    second parameter set has a positive upper slope (without the clamp four of
+    these uniforms land above lambda_max), the third flat branches."""
+    U = np.concatenate([np.arange(1, 2000) * 2.0 ** -53, 1.0 - np.arange(1, 2000) * 2.0 ** -53])
+    for erdf in (ERDF_BASE, np.array([-1.5, 0.0, -0.5, 0.8, 0.1]),
+                 np.array([-3.0, -0.5, -1.0, 0.0, 0.0])):
+        lo, hi = oracle.spec_exp(math.log(10.0) * erdf[:2])
+        for lin in (0, 1):
+            lam = oracle.erdf_icdf(erdf, U, lin)
+            assert lam.min() >= lo and lam.max() <= hi, (erdf, lin)
+            assert lam.min() == pytest.approx(10 ** erdf[0], rel=1e-9)
+            assert lam.max() == pytest.approx(10 ** erdf[1], rel=1e-9)
+
+
 def test_erdf_float_rounding_is_round_to_nearest():
     d64 = oracle.erdf_draws(ERDF_BASE, 4096, 5, 9, prec=1)
     d32 = oracle.erdf_draws(ERDF_BASE, 4096, 5, 9, prec=0)
@@ -350,6 +368,37 @@ def test_iteration_is_a_permutation_and_rank_consistent():
     assert np.all(np.diff(out[order]) >= 0)
 
 
+def test_argsort_orders_ties_like_a_stable_sort():
+    """The rank order is a stable ascending sort: equal keys keep their index
+    order (numpy's stable mergesort as the independent reference)."""
+    rng = np.random.default_rng(21)
+    for v in (rng.integers(0, 7, 5000).astype(np.float64), np.repeat(rng.standard_normal(40), 25),
+              np.zeros(300), np.array([2.0, -0.0, 0.0, -1.0, 0.0, -0.0])):
+        assert np.array_equal(oracle.argsort(v), np.argsort(v, kind="stable"))
+        assert np.array_equal(oracle.sort(v), np.sort(v))
+
+
+def test_pre_ranking_series_has_the_target_amplitudes_and_the_phases_of_the_state():
+    """Sec. 2.1 third step (S96/E13): the series handed to the rank step has,
+    bin for bin, the target amplitudes (A_0 = 0 puts its mean at zero) and the
+    phases of the state it came from; the Nyquist bin is real with the sign of
+    the state's.  Checked with numpy's FFT: rfft(x_adj) = N Y (no 1/N in the
+    inverse)."""
+    log2n = 11
+    n = 1 << log2n
+    _, A = _tk_state(log2n, 6)
+    d = oracle.erdf_draws(ERDF_BASE, n, 6, 0, prec=1)
+    _, xa, _ = oracle.iterate(A, np.sort(d), d, 1, want_adj=True)
+    X = np.fft.rfft(d)
+    Y = np.fft.rfft(xa) / n
+    tol = 1e-12 * np.max(A)
+    assert np.max(np.abs(np.abs(Y) - A)) <= tol
+    assert abs(Y[0]) <= tol and abs(Y[-1].imag) <= tol
+    assert np.sign(Y[-1].real) == (1.0 if X[-1].real >= 0 else -1.0)
+    ph = Y[1:-1] / np.abs(Y[1:-1]) - X[1:-1] / np.abs(X[1:-1])
+    assert np.max(np.abs(ph)) <= 1e-9
+
+
 def test_iteration_brute_force_small():
     """N = 16 against a direct transcription with numpy's FFT and stable argsort."""
     n = 16
@@ -392,7 +441,7 @@ def test_generate_periodogram_follows_psd_shape():
 
 
 def test_batch_equals_single():
-    jobs = [workloads.job(10, 3, seed=c, curve_id=c) for c in range(5)]
+    jobs = [workloads.job(L, 3, seed=c, curve_id=c) for c, L in enumerate((10, 12, 9, 11, 10))]
     x, used = oracle.generate_batch(jobs, prec=0, nthreads=3)
     assert used == 3
     single = np.concatenate([oracle.generate(j, prec=0)["x"] for j in jobs])
