@@ -40,7 +40,8 @@ ALG_BYTES_PER_SAMPLE_ITER = 14  # read x 4 + read A 2 + read s 4 + write x 4 (FP
 # sorted draw and writes the state (16 B).  FP64: 8 passes of 8-byte keys.
 SORT_BYTES_PER_ELEMENT = {4: 12 + 16 + 16 + 16, 8: 20 + 6 * 24 + 28}
 # DRAM bytes (read + write) of the four FP32 scatter passes per element, from
-# one ncu capture of the current kernel (profiles/sort_scatter_uniform_512x2^16.md)
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the four
+# scatter launches of one argsort over 512 curves x 2^16 samples)
 SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 = 1.8893e9 / 2 ** 25
 WORKLOAD = (f"uniform batch: {NCURVES} curves x 2^{LOG2N} samples, dt=1 d, bending PL PSD "
             f"(f_br=1/300 d^-1, slopes 1 and 2), broken-PL ERDF [-4,0] break -1.5 slopes +0.4/-2.5, "
@@ -363,22 +364,34 @@ def run_gpu(args):
         launches_k = 1
         per_launch_bytes = alg_per * prof["fused_elements"]
         kernel = "k_resident_cta / k_resident_cluster (one launch = one iteration of every fused curve)"
+        kernel_bytes_def = f"{alg_per} B per sample-iteration of the fused curves"
     else:
         dominant = "sort_scatter"
         launches_k = max(1, prof["scatter_launches"])
         # every element of every multi-kernel class goes through all passes
         per_launch_bytes = SORT_BYTES_PER_ELEMENT[esize] * prof["sorted_elements"] / launches_k
         kernel = "k_sort_scatter (radix passes of the argsort)"
+        kernel_bytes_def = (f"{SORT_BYTES_PER_ELEMENT[esize]} B per element per argsort (all radix passes), "
+                            "split evenly over the scatter launches")
     avg_ms = prof[dominant] / launches_k
     achieved = per_launch_bytes / (avg_ms / 1000.0) / 1e9
     traffic = None
     if dominant == "sort_scatter" and esize == 4:
         traffic = SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 * prof["sorted_elements"] / launches_k
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": kernel, "launch_ms": avg_ms, "alg_bytes_per_launch": per_launch_bytes,
-            "peak_kind": peak_kind, "group_ms_one_iteration": {g: prof[g] for g in groups},
-            "iteration_stage": {"alg_bytes_per_sample_iter": alg_per, "achieved": stage_gbs,
-                                "frac": stage_gbs / peak, "iterate_ms": it_ms},
+    # The roofline unit is one amplitude-adjustment iteration of every curve
+    # (one replay of the iteration graph): 14 B per sample-iteration (28 B in
+    # FP64) over the iteration stage's CUDA-event time.  The dominant kernel's
+    # figure against its own algorithmic bytes is kept beside it.
+    n_iter = max(1, max(int(j["iters"]) for j in jobs))
+    roof = {"bound": "hbm", "achieved": stage_gbs, "peak": peak, "unit": "GB/s", "frac": stage_gbs / peak,
+            "traffic": None,
+            "kernel": "iteration stage: every kernel of one E13 iteration of every curve (one graph replay)",
+            "alg_bytes_per_sample_iter": alg_per, "alg_bytes_per_launch": alg_per * sample_iters / n_iter,
+            "launch_ms": it_ms / n_iter, "iterate_ms": it_ms, "peak_kind": peak_kind,
+            "dominant_kernel": {"kernel": kernel, "achieved": achieved, "kernel_frac": achieved / peak,
+                                "launch_ms": avg_ms, "alg_bytes_per_launch": per_launch_bytes,
+                                "traffic": traffic, "alg_bytes_definition": kernel_bytes_def},
+            "group_ms_one_iteration": {g: prof[g] for g in groups},
             "setup_ms": setup_ms}
 
     cpu = None

@@ -287,9 +287,10 @@ LC_API lc_status lc_plan_destroy(lc_plan plan);
 
 /* Whole generator for ONE FP32 curve without allocating any device memory.
  * There is no counterpart in the paper: this entry point exists for callers
- * that cannot call cudaMalloc -- code that records into a CUDA stream
- * capture, hosts whose device memory belongs to another allocator, or loops
- * that must not allocate after start-up.  It runs the same kernels as
+ * that cannot call cudaMalloc -- hosts whose device memory belongs to another
+ * allocator (a framework's caching allocator or an accounted memory pool), and
+ * real-time or serving loops that must not allocate after start-up, since a
+ * cudaMalloc can synchronise the device.  It runs the same kernels as
  * lc_generate on a one-curve plan whose buffers all live in a 4 MiB
  * file-scope device array of the library (held by every device that loads
  * the library until the process exits).
@@ -298,8 +299,10 @@ LC_API lc_status lc_plan_destroy(lc_plan plan);
  *   out_x:  device pointer, 2^log2n floats, the final series (caller-owned).
  *   stream: cudaStream_t (NULL = legacy default stream) of the current device.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call reuses the same array and leaves its
+ * (cudaGetSymbolAddress) with that device current and sets the kernels'
+ * shared-memory limits; make that first call before any stream capture.  The
+ * job's descriptor reaches the device as kernel arguments, so no host memory
+ * is read after the call returns.  Every call reuses the same array and leaves its
  * contents behind (each call writes every buffer before reading it, so
  * nothing needs clearing); calls whose work overlaps on the GPU, e.g. on two
  * streams, race on the array and must be serialised by the caller. */

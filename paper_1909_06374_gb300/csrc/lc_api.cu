@@ -45,6 +45,23 @@ void launch_eff_iters(const Plan& p, uint32_t override_iters, cudaStream_t st)
                                                                 p.d_eff_iters, p.d_iter);
 }
 
+lc_status prepare_kernels(int device)
+{
+    static std::mutex mu;
+    static bool done[128];
+    if (device < 0 || device >= 128) { set_error("device ordinal out of range"); return LC_ERR_INVALID; }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[device]) return LC_OK;
+    cudaError_t e = fft_kernel_attributes();
+    if (e == cudaSuccess) e = resident_kernel_attributes();
+    if (e != cudaSuccess) {
+        set_error(std::string("kernel attributes: ") + cudaGetErrorString(e));
+        return LC_ERR_CUDA;
+    }
+    done[device] = true;
+    return LC_OK;
+}
+
 static bool finite(double v) { return std::isfinite(v); }
 
 lc_status validate_job(const lc_job& j)
@@ -136,6 +153,10 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         set_error("no such CUDA device"); return LC_ERR_INVALID;
     }
     DeviceGuard g(device);
+    {
+        const lc_status ps = prepare_kernels(device);
+        if (ps != LC_OK) return ps;
+    }
     Plan* p = new (std::nothrow) Plan();
     if (!p) return LC_ERR_NOMEM;
     p->device = device;

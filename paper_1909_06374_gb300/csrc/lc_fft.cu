@@ -629,12 +629,55 @@ bool tile_schedule_ok(uint32_t log2M, bool fp64)
     return (1u << (log2M - Ls)) >= (uint32_t)tile_cols(Ls, eb);
 }
 
+// Dynamic shared memory of one tile-kernel launch (k_fft_tile, k_fft_spectral)
+// of radix 2^LR on a length-2^log2M transform: the tile (R rows of C + 1
+// elements) and the twiddle tables.  Grows with log2M.
+template <typename T>
+static size_t tile_smem_bytes(int LR, int log2M)
+{
+    return (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries(log2M, LR)) *
+           sizeof(cplx<T>);
+}
+
+// The longest transform of the tile path: M = 2^26 (N = 2^27).
+constexpr int kTileMaxLog2M = 26;
+
+template <typename T, int LR>
+static cudaError_t tile_attrs()
+{
+    const int smem = (int)tile_smem_bytes<T>(LR, kTileMaxLog2M);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_tile<T, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_tile<T, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_spectral<T, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+// Raises the dynamic shared-memory limit of every tile-kernel instantiation
+// to what its longest transform needs, once per device (see
+// prepare_kernels).  One limit per function for all lengths: a graph that
+// holds launches of one instantiation for several lengths, or a kernel node
+// replayed on its own, never asks for more than the function allows.
+cudaError_t fft_kernel_attributes()
+{
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = tile_attrs<float, 5>();
+    if (e == cudaSuccess) e = tile_attrs<float, 6>();
+    if (e == cudaSuccess) e = tile_attrs<float, 7>();
+    if (e == cudaSuccess) e = tile_attrs<float, 8>();
+    if (e == cudaSuccess) e = tile_attrs<float, 9>();
+    if (e == cudaSuccess) e = tile_attrs<double, 5>();
+    if (e == cudaSuccess) e = tile_attrs<double, 6>();
+    if (e == cudaSuccess) e = tile_attrs<double, 7>();
+    if (e == cudaSuccess) e = tile_attrs<double, 8>();
+    return e;
+}
+
 template <typename T, int LR, bool INV>
 static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
 {
-    const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M, LR)) * sizeof(cplx<T>);
-    cudaFuncSetAttribute(k_fft_tile<T, LR, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fft_tile<T, LR, INV><<<blocks, 256, smem, st>>>(a);
+    k_fft_tile<T, LR, INV><<<blocks, 256, tile_smem_bytes<T>(LR, (int)a.log2M), st>>>(a);
 }
 
 template <typename T, bool INV>
@@ -767,12 +810,11 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
     a.in = cur; a.out = nxt; a.log2p = log2p;
     {
         const int blocks = tile_blocks<T>(k.ncurves, a.log2M, LR);
-        const size_t smem = (((size_t)1 << LR) * (tile_cols(LR, (int)sizeof(cplx<T>)) + 1) + smem_tw_entries((int)a.log2M, LR)) * sizeof(cplx<T>);
+        const size_t smem = tile_smem_bytes<T>(LR, (int)a.log2M);
         switch (LR) {
-#define LC_FUSED_CASE(L)                                                                                   \
-    case L:                                                                                                \
-        cudaFuncSetAttribute(k_fft_spectral<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k_fft_spectral<T, L><<<blocks, 256, smem, st>>>(a, p.d_A);                                          \
+#define LC_FUSED_CASE(L)                                            \
+    case L:                                                         \
+        k_fft_spectral<T, L><<<blocks, 256, smem, st>>>(a, p.d_A); \
         break;
             LC_FUSED_CASE(5)
             LC_FUSED_CASE(6)
@@ -781,7 +823,6 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
 #undef LC_FUSED_CASE
         default:
             if (sizeof(T) == 4 && LR == 9) {
-                cudaFuncSetAttribute(k_fft_spectral<float, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 k_fft_spectral<float, 9><<<blocks, 256, smem, st>>>(a, p.d_A);
             } else {
                 set_error("internal: unsupported fused radix");

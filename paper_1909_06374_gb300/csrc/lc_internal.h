@@ -203,6 +203,13 @@ void launch_iter_increment(const Plan& p, cudaStream_t st);
 void launch_iter_add(const Plan& p, uint32_t n, cudaStream_t st);
 void launch_eff_iters(const Plan& p, uint32_t override_iters, cudaStream_t st);
 
+// Kernel attributes that are set once per device before the first launch
+// (dynamic shared-memory limits of the tile FFT and fused kernels); the
+// device must be current.  LC_ERR_CUDA with the error text on failure.
+cudaError_t fft_kernel_attributes();
+cudaError_t resident_kernel_attributes();
+lc_status prepare_kernels(int device);
+
 void set_error(const std::string& msg);
 const char* last_error_text();
 lc_status validate_job(const lc_job& j);

@@ -1,11 +1,13 @@
 // lc_noalloc.cu -- single-curve generator entry point that allocates nothing.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA stream
-// capture that must not add allocation nodes, embedders whose device memory is
-// owned by another allocator, or real-time loops that forbid allocation after
-// start-up.  lc_generate_noalloc runs the whole generator for one FP32 curve of
-// up to 2^16 samples with every intermediate buffer carved from one
-// file-scope device array; the caller passes only the job and the output.
+// Some callers cannot call cudaMalloc: embedders whose device memory is owned
+// by another allocator (a framework's caching allocator or a memory pool that
+// must account for every byte), and real-time or serving loops that forbid
+// allocation after start-up because a cudaMalloc can synchronise the device
+// and stall unrelated work.  lc_generate_noalloc runs the whole generator for
+// one FP32 curve of up to 2^16 samples with every intermediate buffer carved
+// from one file-scope device array; the caller passes only the job and the
+// output.
 #include <mutex>
 
 #include "lc_internal.h"
@@ -44,6 +46,14 @@ static lc_status noalloc_scratch(int dev, void** out)
 
 static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
+// Writes the curve descriptor and the class's curve index from kernel
+// arguments (copied at launch), so no host memory is read after the call.
+__global__ void k_noalloc_descriptors(CurveDev cv, CurveDev* __restrict__ d_cv, int* __restrict__ d_cls)
+{
+    *d_cv = cv;
+    *d_cls = 0;
+}
+
 }  // namespace lc
 
 using namespace lc;
@@ -59,6 +69,8 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); set_error("no current CUDA device"); return LC_ERR_CUDA; }
+    st = prepare_kernels(dev);
+    if (st != LC_OK) return st;
     void* base = nullptr;
     st = noalloc_scratch(dev, &base);
     if (st != LC_OK) return st;
@@ -124,13 +136,7 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     }
     if (at > kNoallocBytes) { set_error("lc_generate_noalloc: layout exceeds the static scratch"); return LC_ERR_INVALID; }
 
-    // descriptors (pageable host source: the copy is staged before the call returns)
-    const int zero = 0;
-    if (cudaMemcpyAsync(p.d_curves, &cv, sizeof(CurveDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(k.d_curves, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        set_error("descriptor upload failed");
-        return LC_ERR_CUDA;
-    }
+    k_noalloc_descriptors<<<1, 1, 0, s>>>(cv, p.d_curves, k.d_curves);
     launch_twiddles<float>(k, s);
     // setup: TK95 spectrum and amplitudes, ERDF draws, sorted draws (Sec. 2.1)
     launch_eff_iters(p, 0, s);

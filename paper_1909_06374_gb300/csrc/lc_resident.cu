@@ -623,35 +623,53 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kResThreads, 1) k_re
     }
 }
 
-template <int LOG2L, bool CONV>
-void launch_cta_mode(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
-{
-    cudaFuncSetAttribute(k_resident_cta<LOG2L, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    k_resident_cta<LOG2L, CONV><<<ncurves, kResThreads, smem, st>>>(a);
-}
-
 template <int LOG2L>
-void launch_cta(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
+void launch_cta(const ResArgs& a, int ncurves, size_t smem, cudaStream_t st)
 {
-    if (a.conv.delta) launch_cta_mode<LOG2L, true>(a, ncurves, smem, smax, st);
-    else launch_cta_mode<LOG2L, false>(a, ncurves, smem, smax, st);
-}
-
-template <int C, bool CONV>
-void launch_cluster_mode(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
-{
-    cudaFuncSetAttribute(k_resident_cluster<C, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    k_resident_cluster<C, CONV><<<ncurves * C, kResThreads, smem, st>>>(a);
+    if (a.conv.delta) k_resident_cta<LOG2L, true><<<ncurves, kResThreads, smem, st>>>(a);
+    else k_resident_cta<LOG2L, false><<<ncurves, kResThreads, smem, st>>>(a);
 }
 
 template <int C>
-void launch_cluster(const ResArgs& a, int ncurves, size_t smem, int smax, cudaStream_t st)
+void launch_cluster(const ResArgs& a, int ncurves, size_t smem, cudaStream_t st)
 {
-    if (a.conv.delta) launch_cluster_mode<C, true>(a, ncurves, smem, smax, st);
-    else launch_cluster_mode<C, false>(a, ncurves, smem, smax, st);
+    if (a.conv.delta) k_resident_cluster<C, true><<<ncurves * C, kResThreads, smem, st>>>(a);
+    else k_resident_cluster<C, false><<<ncurves * C, kResThreads, smem, st>>>(a);
+}
+
+// Shared memory of the fused kernels at their longest one-CTA length (the
+// cluster kernels hold the same per CTA).
+constexpr size_t kResSmemMax = 12 * ((size_t)1 << kResMaxLog2) + kWhBytes + kTwBytes;
+
+template <typename F>
+cudaError_t res_attr(F* f)
+{
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmemMax);
 }
 
 }  // namespace
+
+// Every fused-kernel instantiation may use up to kResSmemMax bytes of dynamic
+// shared memory; set once per device (see prepare_kernels).
+cudaError_t resident_kernel_attributes()
+{
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<10, false>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<10, true>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<11, false>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<11, true>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<12, false>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<12, true>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<13, false>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<13, true>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<14, false>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cta<14, true>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cluster<2, false>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cluster<2, true>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cluster<4, false>);
+    if (e == cudaSuccess) e = res_attr(k_resident_cluster<4, true>);
+    return e;
+}
 
 // Path table (measured on GB300, 2^28 samples x 200 iterations per length,
 // sample*iter/s): the one-CTA fused kernel wins from 2^10 to 2^14 (2^12:
@@ -692,19 +710,18 @@ void launch_resident(const Plan& p, const ClassInfo& k, uint32_t n_it, cudaStrea
     const int C = k.log2n <= kResMaxLog2 ? 1 : 1 << (k.log2n - kResMaxLog2);
     const size_t L = ((size_t)1 << k.log2n) / C;
     const size_t smem = 12 * L + kWhBytes + kTwBytes;
-    const int smax = (int)(12 * ((size_t)1 << kResMaxLog2) + kWhBytes + kTwBytes);
     if (C == 1) {
         switch (k.log2n) {
-        case 10: launch_cta<10>(a, k.ncurves, smem, smax, st); break;
-        case 11: launch_cta<11>(a, k.ncurves, smem, smax, st); break;
-        case 12: launch_cta<12>(a, k.ncurves, smem, smax, st); break;
-        case 13: launch_cta<13>(a, k.ncurves, smem, smax, st); break;
-        default: launch_cta<14>(a, k.ncurves, smem, smax, st); break;
+        case 10: launch_cta<10>(a, k.ncurves, smem, st); break;
+        case 11: launch_cta<11>(a, k.ncurves, smem, st); break;
+        case 12: launch_cta<12>(a, k.ncurves, smem, st); break;
+        case 13: launch_cta<13>(a, k.ncurves, smem, st); break;
+        default: launch_cta<14>(a, k.ncurves, smem, st); break;
         }
     } else if (C == 2) {
-        launch_cluster<2>(a, k.ncurves, smem, smax, st);
+        launch_cluster<2>(a, k.ncurves, smem, st);
     } else {
-        launch_cluster<4>(a, k.ncurves, smem, smax, st);
+        launch_cluster<4>(a, k.ncurves, smem, st);
     }
     if (launches) ++*launches;
 }

@@ -380,3 +380,31 @@ def test_profile_runs_one_iteration_with_timed_groups():
     assert prof["convergence"] == 0
     assert prof["scatter_launches"] == 2 * 4  # two multi-kernel classes, four FP32 radix passes
     assert prof["sorted_elements"] == (1 << 17) + (1 << 9) and prof["fused_elements"] == 1 << 12
+
+
+def test_classes_sharing_tile_kernels_one_step():
+    """Curves of 2^18, 2^16 and 2^17 samples in one plan: the 2^18 and 2^17
+    classes run the fused forward-last / spectral / inverse-first kernel of
+    radix 2^8, the 2^16 and 2^17 classes the radix-2^8 tile pass, each with a
+    different shared-memory size (the twiddle tables grow with the length).
+    Every launch of the captured iteration graph must get the size it asks
+    for.  One iteration from the oracle's state, per position, on all three
+    (the oracle's states after one of its iterations)."""
+    jobs = [workloads.job(18, 3, seed=51, curve_id=0, f_br=0.01),
+            workloads.job(16, 3, seed=52, curve_id=1),
+            workloads.job(17, 3, seed=53, curve_id=2, alpha_high=2.7)]
+    states, expect = [], []
+    for j in jobs:
+        r = oracle.generate(dict(j, iters=0), prec=0, want=("x", "A", "s"))
+        xk, _, _ = oracle.iterate(r["A"], r["s"], r["x"], 1)
+        x1, xa, _ = oracle.iterate(r["A"], r["s"], xk, 1, want_adj=True)
+        states.append(xk)
+        expect.append((x1, r["s"], xa))
+    with Plan(jobs, LC_FP32) as p:
+        p.generate()  # the iteration graph is captured and replayed first
+        p.set_state(torch.tensor(np.concatenate(states), dtype=torch.float32, device="cuda"))
+        p.iterate(1)
+        got = _np(p.get_state())
+    for c, (x1, s, xa) in enumerate(expect):
+        r = position_check(got[p.offsets[c]:p.offsets[c + 1]], x1, s, xa)
+        assert r["fail"] == 0 and r["not_in_draws"] == 0, (jobs[c]["log2n"], r)

@@ -1,7 +1,7 @@
-"""The allocation-free entry point (for callers that cannot call cudaMalloc,
-e.g. inside a stream capture or under another allocator) against the ordinary
-batch entry point, through the C ABI, on consecutive calls that reuse its
-static device array."""
+"""The allocation-free entry point (for callers that cannot call cudaMalloc:
+hosts whose device memory belongs to another allocator, or loops that must not
+allocate after start-up) against the ordinary batch entry point, through the C
+ABI, on consecutive calls that reuse its static device array."""
 import ctypes
 
 import numpy as np
