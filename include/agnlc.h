@@ -186,6 +186,21 @@ LC_API lc_status lc_iterate(lc_plan plan, uint32_t iters, void* stream);
 LC_API lc_status lc_get_state(lc_plan plan, void* out_x, void* stream);
 LC_API lc_status lc_set_state(lc_plan plan, const void* in_x, void* stream);
 
+/* The rank-order replacement step of one iteration on its own (Sec. 2.1,
+ * third step; Sec. 3.2.2: the values stay the sorted draws, only their order
+ * changes): for every curve c, out_x[perm_c[r]] = s_c[r] for r < N_c, where
+ * s_c are the curve's sorted draws and perm_c the stable ascending argsort of
+ * x_adj's curve c (ties, -0 = +0 included, keep the lower position first).
+ * The plan's own sort path runs (the sample sort of FP32 curves of 2^13 ..
+ * 2^18 samples, else the LSD radix passes).
+ *   x_adj: device pointer, sum_c N_c elements in the plan's precision and
+ *          layout (curve c at the offset of lc_get_state); read only; values
+ *          must not be NaN.
+ *   out_x: device pointer, same size and layout (caller-owned); may be x_adj.
+ * Requires lc_setup or lc_generate before (for s); the plan's state is not
+ * touched.  Asynchronous on `stream`. */
+LC_API lc_status lc_rank_replace(lc_plan plan, const void* x_adj, void* out_x, void* stream);
+
 /* Read-only view of a plan buffer, valid until lc_plan_destroy:
  * which = 0: state x (sum N elements); 1: target amplitudes A
  * (sum (N/2+1) elements, curve c at sum_{c'<c} (N_{c'}/2+1)); 2: sorted
@@ -270,12 +285,15 @@ LC_API lc_status lc_structure_function(lc_plan plan, const void* x, const uint32
  * graph) with CUDA events on the plan's stream around each kernel group, and
  * returns the device milliseconds per group:
  *   group_ms[0] transforms and spectral step (multi-kernel path),
- *   group_ms[1] sort histograms and scans, group_ms[2] sort scatter passes,
- *   group_ms[3] fused on-chip kernels, group_ms[4] convergence test.
+ *   group_ms[1] sort histograms and scans (sample sort: sample, histogram
+ *   and scan kernels), group_ms[2] sort scatter passes (sample sort: bucket
+ *   scatter and on-chip finish), group_ms[3] fused on-chip kernels,
+ *   group_ms[4] convergence test.
  * ngroups: entries of group_ms to fill (extra ones get 0).
- * counts (nullable, 3 entries): scatter launches timed, samples of the
- * multi-kernel classes (each goes through every scatter pass), samples of
- * the fused classes.
+ * counts (nullable, 4 entries): scatter spans timed (one per radix pass of
+ * each radix-sorted class, one per sample-sorted class), samples of the
+ * multi-kernel classes, samples of the fused classes, samples of the
+ * multi-kernel classes whose argsort is the sample sort.
  * The state advances by one iteration; the iteration counter restarts, so a
  * later lc_iterate(plan, 0) runs each job's count again.  Blocking. */
 LC_API lc_status lc_plan_profile(lc_plan plan, float* group_ms, size_t ngroups, uint64_t* counts);

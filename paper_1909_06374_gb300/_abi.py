@@ -62,6 +62,7 @@ _SIGS = {
     "lc_iterate": (c_i32, [c_p, c_u32, c_p]),
     "lc_get_state": (c_i32, [c_p, c_p, c_p]),
     "lc_set_state": (c_i32, [c_p, c_p, c_p]),
+    "lc_rank_replace": (c_i32, [c_p, c_p, c_p, c_p]),
     "lc_plan_buffer": (c_i32, [c_p, c_i32, ctypes.POINTER(c_p), ctypes.POINTER(c_sz)]),
     "lc_plan_last_launches": (c_i32, [c_p, ctypes.POINTER(c_u64)]),
     "lc_plan_timing": (c_i32, [c_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -204,6 +205,10 @@ def lc_set_state(plan, in_x, stream=None):
     _check(load().lc_set_state(plan, ptr(in_x), stream_ptr(stream)), "lc_set_state")
 
 
+def lc_rank_replace(plan, x_adj, out_x, stream=None):
+    _check(load().lc_rank_replace(plan, ptr(x_adj), ptr(out_x), stream_ptr(stream)), "lc_rank_replace")
+
+
 def lc_plan_buffer(plan, which):
     p, n = c_p(), c_sz()
     _check(load().lc_plan_buffer(plan, int(which), ctypes.byref(p), ctypes.byref(n)), "lc_plan_buffer")
@@ -256,11 +261,12 @@ def lc_structure_function(plan, x, lags, out_sf2, stream=None):
 def lc_plan_profile(plan):
     """Per-group device ms of one extra iteration (see agnlc.h) as a dict."""
     ms = (ctypes.c_float * 5)()
-    cnt = (c_u64 * 3)()
+    cnt = (c_u64 * 4)()
     _check(load().lc_plan_profile(plan, ms, 5, cnt), "lc_plan_profile")
     names = ("fft", "sort_hist_scan", "sort_scatter", "resident", "convergence")
     out = {n: float(v) for n, v in zip(names, ms)}
     out["scatter_launches"], out["sorted_elements"], out["fused_elements"] = int(cnt[0]), int(cnt[1]), int(cnt[2])
+    out["bucket_elements"] = int(cnt[3])
     return out
 
 

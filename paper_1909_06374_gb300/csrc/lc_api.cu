@@ -54,6 +54,7 @@ lc_status prepare_kernels(int device)
     if (done[device]) return LC_OK;
     cudaError_t e = fft_kernel_attributes();
     if (e == cudaSuccess) e = resident_kernel_attributes();
+    if (e == cudaSuccess) e = bucket_kernel_attributes();
     if (e != cudaSuccess) {
         set_error(std::string("kernel attributes: ") + cudaGetErrorString(e));
         return LC_ERR_CUDA;
@@ -209,9 +210,12 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         }
     }
     // arena layout
-    size_t hist = 0, cbase = 0, partial = 0, twb = 0, rxb = 0;
+    size_t hist = 0, cbase = 0, partial = 0, twb = 0, rxb = 0, auxb = 0;
+    const bool bucket_on = bucket_enabled_from_env();
     for (auto& k : p->classes) {
         k.ncurves = (int)k.h_curves.size();
+        k.bucket = bucket_on && bucket_supported(prec, k.log2n);
+        if (k.bucket) auxb += align_up((size_t)k.ncurves * bucket_aux_words(k.log2n) * 4, 256);
         k.radices = fft_radices(k.log2n - 1);
         const size_t n = 1ull << k.log2n;
         k.tile_len = (int)std::min<size_t>(n, kSortTile);
@@ -246,6 +250,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     const size_t o_tabc = take(sizeof(int) * 2 * p->ntab);  // all, then per class
     const size_t o_tab = take(sizeof(double) * (kErdfTable + 1) * p->ntab);
     const size_t o_rx = prec == LC_FP32 ? take(rxb) : 0;
+    const size_t o_aux = take(auxb);
     p->arena_bytes = sz;
     if (cudaMalloc(&p->arena, sz) != cudaSuccess) {
         cudaGetLastError();
@@ -273,8 +278,12 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->d_spec = (double2*)(base + o_sort);
     p->d_hist = (uint32_t*)(base + o_hist);
     p->d_cbase = (uint32_t*)(base + o_cbase);
-    size_t tw_at = o_tw, cls_at = o_cls, rx_at = o_rx;
+    size_t tw_at = o_tw, cls_at = o_cls, rx_at = o_rx, aux_at = o_aux;
     for (auto& k : p->classes) {
+        if (k.bucket) {
+            k.d_aux = (uint32_t*)(base + aux_at);
+            aux_at += align_up((size_t)k.ncurves * bucket_aux_words(k.log2n) * 4, 256);
+        }
         k.d_tw = base + tw_at;
         tw_at += align_up((((size_t)1 << k.log2n) / 2) * 2 * ts, 256);
         k.d_curves = (int*)(base + cls_at);
@@ -635,6 +644,27 @@ lc_status lc_set_state(lc_plan plan, const void* in_x, void* stream)
     return LC_OK;
 }
 
+lc_status lc_rank_replace(lc_plan plan, const void* x_adj, void* out_x, void* stream)
+{
+    if (!plan || !x_adj || !out_x) { set_error("null argument"); return LC_ERR_INVALID; }
+    if (!plan->setup_done) { set_error("lc_rank_replace before lc_setup/lc_generate"); return LC_ERR_INVALID; }
+    DeviceGuard g(plan->device);
+    StreamJoin j(*plan, stream);
+    const size_t ts = plan->prec == LC_FP32 ? 4 : 8;
+    // the sort reads its values from the FFT buffer, as in an iteration
+    LC_CK(cudaMemcpyAsync(plan->d_f, x_adj, plan->total * ts, cudaMemcpyDeviceToDevice, plan->stream));
+    uint64_t n = 0;
+    for (auto& k : plan->classes) {
+        if (plan->prec == LC_FP32)
+            launch_sort<float>(*plan, k, plan->d_f, kSortArgsortScatter, false, plan->stream, &n, out_x);
+        else
+            launch_sort<double>(*plan, k, plan->d_f, kSortArgsortScatter, false, plan->stream, &n, out_x);
+    }
+    plan->last_launches = n + 1;
+    LC_CK(cudaGetLastError());
+    return LC_OK;
+}
+
 lc_status lc_plan_buffer(lc_plan plan, int which, const void** device_ptr, size_t* bytes)
 {
     if (!plan || !device_ptr) { set_error("null argument"); return LC_ERR_INVALID; }
@@ -782,10 +812,14 @@ lc_status lc_plan_profile(lc_plan plan, float* group_ms, size_t ngroups, uint64_
         if (counts) counts[0] = nscatter;
     }
     if (counts) {
-        uint64_t multi = 0, fused = 0;
-        for (auto& k : p.classes) (k.resident ? fused : multi) += (uint64_t)k.ncurves << k.log2n;
+        uint64_t multi = 0, fused = 0, bucket = 0;
+        for (auto& k : p.classes) {
+            (k.resident ? fused : multi) += (uint64_t)k.ncurves << k.log2n;
+            if (!k.resident && k.bucket) bucket += (uint64_t)k.ncurves << k.log2n;
+        }
         counts[1] = multi;
         counts[2] = fused;
+        counts[3] = bucket;
     }
     p.timed_iter = false;
     return LC_OK;

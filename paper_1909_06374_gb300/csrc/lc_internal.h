@@ -30,6 +30,8 @@ struct ClassInfo {
     size_t partial_off = 0;            // into d_partial (double)
     bool resident = false;             // iterated by the fused on-chip kernel
     float* d_rx = nullptr;             // L2 exchange area of the cluster kernel (3 N floats per curve)
+    bool bucket = false;               // argsort by the sample sort of lc_bucket.cu
+    uint32_t* d_aux = nullptr;         // its per-curve splitters, bases and groups
     int ntab = 0;                      // curves with a tabulated ERDF (Eq. 1 smooth, Eq. 2)
     int* d_tab_curves = nullptr;       // their curve indices (device)
     std::vector<int> h_tab_curves;
@@ -175,6 +177,21 @@ enum SortMode { kSortArgsortScatter = 1, kSortKeysToValues = 2 };
 template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode,
                                        bool gated, cudaStream_t st, uint64_t* launches, void* x_out = nullptr,
                                        KernelTimes* kt = nullptr);
+// sample-sort argsort of the iteration (lc_bucket.cu): FP32 curves of
+// 2^kBkMinLog2 .. 2^kBkMaxLog2 samples; groups of at most kBkCap elements are
+// ranked in shared memory
+constexpr int kBkCap = 4096;
+constexpr uint32_t kBkMinLog2 = 13;
+constexpr uint32_t kBkMaxLog2 = 18;
+bool bucket_supported(lc_precision prec, uint32_t log2n);
+// LC_SORT=radix keeps the LSD radix argsort for every length
+bool bucket_enabled_from_env();
+int bucket_gmax(uint32_t log2n);
+size_t bucket_aux_words(uint32_t log2n);  // u32 words per curve
+cudaError_t bucket_kernel_attributes();
+// x_out[perm[r]] = s[r] with perm the stable argsort of `src` (gated).
+void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, void* x_out, bool gated,
+                           cudaStream_t st, uint64_t* launches, KernelTimes* kt);
 // Eq. 4 partial sums of a multi-kernel class between the state x_{i-1} and
 // the new iterate x_i in `xnew` (one double per sort tile, curve-major, in
 // conv.part), moving x_i into the state; for launch_conv_finalize.

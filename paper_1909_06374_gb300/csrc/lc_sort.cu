@@ -534,6 +534,10 @@ template <typename T>
 void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode, bool gated,
                  cudaStream_t st, uint64_t* launches, void* x_out, KernelTimes* kt)
 {
+    if (mode == kSortArgsortScatter && k.bucket) {
+        launch_bucket_argsort(p, k, src, x_out, gated, st, launches, kt);
+        return;
+    }
     using K = typename key_of<T>::type;
     const int passes = (int)sizeof(K);  // 8-bit digits
     SortArgs a{};

@@ -378,8 +378,10 @@ def test_profile_runs_one_iteration_with_timed_groups():
     assert np.array_equal(after, want)
     assert prof["resident"] > 0 and prof["fft"] > 0 and prof["sort_scatter"] > 0 and prof["sort_hist_scan"] > 0
     assert prof["convergence"] == 0
-    assert prof["scatter_launches"] == 2 * 4  # two multi-kernel classes, four FP32 radix passes
+    # the 2^9 class: four FP32 radix passes; the 2^17 class: the sample sort (one span)
+    assert prof["scatter_launches"] == 4 + 1
     assert prof["sorted_elements"] == (1 << 17) + (1 << 9) and prof["fused_elements"] == 1 << 12
+    assert prof["bucket_elements"] == 1 << 17
 
 
 def test_classes_sharing_tile_kernels_one_step():
