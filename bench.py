@@ -39,10 +39,10 @@ ALG_BYTES_PER_SAMPLE_ITER = 14  # read x 4 + read A 2 + read s 4 + write x 4 (FP
 # write key + position (16 B each), the last reads key + position and the
 # sorted draw and writes the state (16 B).  FP64: 8 passes of 8-byte keys.
 SORT_BYTES_PER_ELEMENT = {4: 12 + 16 + 16 + 16, 8: 20 + 6 * 24 + 28}
-# The sample sort's scatter group (FP32): the bucket scatter reads the value and
-# writes value + position (12 B), the on-chip finish reads them back, gathers
-# the sorted draw and writes the state (16 B).
-BUCKET_SCATTER_BYTES_PER_ELEMENT = 12 + 16
+# The sample sort's scatter group (FP32): the bucket scatter reads the value and its
+# bucket byte and writes value + position (13 B), the on-chip finish reads them
+# back, reads the sorted draws and writes the state (16 B).
+BUCKET_SCATTER_BYTES_PER_ELEMENT = 13 + 16
 # DRAM bytes (read + write) of the four FP32 scatter passes per element, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the four
 # scatter launches of one argsort over 512 curves x 2^16 samples)
@@ -379,7 +379,7 @@ def run_gpu(args):
         per_launch_bytes = (SORT_BYTES_PER_ELEMENT[esize] * nr + BUCKET_SCATTER_BYTES_PER_ELEMENT * nb) / launches_k
         if nb and not nr:
             kernel = "k_bk_scatter + k_bk_finish (sample-sort argsort: bucket scatter and on-chip ranking)"
-            kernel_bytes_def = f"{BUCKET_SCATTER_BYTES_PER_ELEMENT} B per element (scatter 12 + finish 16)"
+            kernel_bytes_def = f"{BUCKET_SCATTER_BYTES_PER_ELEMENT} B per element (scatter 13 + finish 16)"
         else:
             kernel = "k_sort_scatter (radix passes of the argsort)" + (" and the sample-sort scatter" if nb else "")
             kernel_bytes_def = (f"{SORT_BYTES_PER_ELEMENT[esize]} B per element per radix argsort (all passes), "

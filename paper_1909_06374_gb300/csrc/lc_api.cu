@@ -215,7 +215,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     for (auto& k : p->classes) {
         k.ncurves = (int)k.h_curves.size();
         k.bucket = bucket_on && bucket_supported(prec, k.log2n);
-        if (k.bucket) auxb += align_up((size_t)k.ncurves * bucket_aux_words(k.log2n) * 4, 256);
+        if (k.bucket) auxb += align_up(bucket_aux_words(k.log2n, k.ncurves) * 4, 256);
         k.radices = fft_radices(k.log2n - 1);
         const size_t n = 1ull << k.log2n;
         k.tile_len = (int)std::min<size_t>(n, kSortTile);
@@ -282,7 +282,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     for (auto& k : p->classes) {
         if (k.bucket) {
             k.d_aux = (uint32_t*)(base + aux_at);
-            aux_at += align_up((size_t)k.ncurves * bucket_aux_words(k.log2n) * 4, 256);
+            aux_at += align_up(bucket_aux_words(k.log2n, k.ncurves) * 4, 256);
         }
         k.d_tw = base + tw_at;
         tw_at += align_up((((size_t)1 << k.log2n) / 2) * 2 * ts, 256);

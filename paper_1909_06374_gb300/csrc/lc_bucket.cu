@@ -3,32 +3,35 @@
 // x_adj) as a sample sort: one bucket pass through HBM and one on-chip pass
 // that ranks every element exactly.
 //
-// Per curve of N = 2^13 .. 2^18 FP32 samples:
+// Per curve of N = 2^13 .. 2^17 FP32 samples:
 //   k_bk_sample   1024 values of x_adj at a fixed stride, sorted in shared
 //                 memory; 255 of them become the splitters of 256 buckets
 //                 (bucket b holds spl[b-1] <= x < spl[b]);
 //   k_bk_hist     per 2048-element tile: bucket of every element (binary
-//                 search over the splitters) and the tile's bucket counts;
-//                 the curve's minimum and maximum;
-//   k_bk_scan     tile prefixes and bucket bases of the curve, and groups of
-//                 consecutive buckets of at most kBkCap elements;
-//   k_bk_scatter  every element (value, position | bucket << 24) into its
-//                 tile's slice of its bucket (shared-memory atomics: the
-//                 order inside a slice is arbitrary);
-//   k_bk_finish   one group per block, in shared memory: each bucket is split
-//                 into as many sub-buckets as it has elements by linear
+//                 search over the splitters; one byte per element kept for
+//                 the scatter) and the tile's bucket counts; the curve's
+//                 minimum and maximum;
+//   k_bk_scan     tile prefixes and bucket bases of the curve, each bucket's
+//                 bounds, and groups of consecutive buckets of at most kBkCap
+//                 elements, appended to the class's list of work items;
+//   k_bk_scatter  per tile: the elements placed in shared memory in bucket
+//                 order (the order inside a bucket is arbitrary), then each
+//                 bucket's run written to the tile's slice of the bucket;
+//   k_bk_finish   one work item per block, in shared memory: every bucket is
+//                 split into two sub-buckets per element by linear
 //                 interpolation of the value between the bucket's bounds
 //                 (monotone), the group is counting-sorted by sub-bucket, and
-//                 every element is ranked among the members of its sub-bucket
-//                 by (value, position) -- the stable argsort order, whatever
-//                 order the scatter left.  rank = bucket base + rank in group;
-//                 the block writes x[position] = s[rank].
+//                 an element that shares its sub-bucket is ranked among its
+//                 members by (value, position) -- the stable argsort order,
+//                 whatever order the scatter left.  rank = group base + rank
+//                 in the group; the block writes x[position] = s[rank].
 // A bucket of more than kBkCap elements (a spike of equal or nearly equal
 // values) is one group of its own, sorted by a block-level LSD radix sort on
 // (value, position) through global memory instead.
 //
-// HBM bytes per element: 4 (histogram) + 4 + 8 (scatter) + 8 + 4 + 4 (finish)
-// = 32, against 76 for the four 8-bit LSD passes and their histograms.
+// HBM bytes per element: 4 (histogram) + 4 + 1 + 8 (scatter, incl. the
+// bucket byte) + 8 + 4 + 4 (finish) + 1 (bucket byte written) = 34, against
+// 76 for the four 8-bit LSD passes and their histograms.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -39,20 +42,26 @@ namespace lc {
 
 constexpr int kBkBuckets = 256;
 constexpr int kBkSample = 1024;
-constexpr int kBkThreads = 512;                  // sample and finish kernels
+constexpr int kBkSampleThreads = 512;
+constexpr int kBkThreads = 256;                  // finish kernel
 constexpr int kBkPer = kBkCap / kBkThreads;      // elements per finish thread
 constexpr int kBkTileThreads = 256;              // histogram and scatter kernels
-constexpr int kBkTilePer = kSortTile / kBkTileThreads;  // 8 elements per thread and tile
 
-// Per-curve words of the auxiliary area (u32): splitters (float bits), the
-// curve's min and max (order keys), bucket bases (257), then the group count
-// and the group starts (bucket indices, gmax + 1).
+// Auxiliary area of a class (u32 words): a 64-word header (word 0: the
+// number of work items appended this iteration), then per curve: splitters
+// (float bits), the curve's min and max (order keys), bucket bases (257), the
+// group count, per-bucket parameters (lower bound, elements per unit value,
+// base, count: 4 words each); then the work items of the finish kernel, one
+// per group (e0, n, first bucket, buckets; curve offset lo, hi, class index
+// of the curve, 0: 8 words each), appended in any order.
+constexpr int kAuxHeader = 64;
 constexpr int kAuxSpl = 0;
 constexpr int kAuxMin = 256;
 constexpr int kAuxMax = 257;
 constexpr int kAuxBase = 258;
 constexpr int kAuxGcount = kAuxBase + kBkBuckets + 1;   // 515
-constexpr int kAuxGstart = kAuxGcount + 1;              // 516
+constexpr int kAuxPar = 516;                            // 16-byte aligned
+constexpr int kAuxCurveWords = ((kAuxPar + 4 * kBkBuckets) + 63) / 64 * 64;
 
 int bucket_gmax(uint32_t log2n)
 {
@@ -60,10 +69,9 @@ int bucket_gmax(uint32_t log2n)
     return 2 * (int)(((size_t)1 << log2n) / kBkCap) + 1;
 }
 
-size_t bucket_aux_words(uint32_t log2n)
+size_t bucket_aux_words(uint32_t log2n, int ncurves)
 {
-    const size_t w = (size_t)kAuxGstart + (size_t)bucket_gmax(log2n) + 1;
-    return (w + 63) / 64 * 64;
+    return (size_t)kAuxHeader + (size_t)ncurves * kAuxCurveWords + 8 * (size_t)ncurves * bucket_gmax(log2n);
 }
 
 bool bucket_supported(lc_precision prec, uint32_t log2n)
@@ -83,8 +91,11 @@ struct BkArgs {
     const uint32_t* eff_iters;
     const int* d_iter;       // null: every curve active
     const float* xadj;       // values to rank (the inverse transform's output)
-    uint32_t* aux;           // [ci][stride]
+    uint32_t* aux;           // [ci][kAuxCurveWords]
+    uint32_t* nitems;        // work items appended this iteration
+    uint4* items;            // [2 * item]: e0, n, first bucket, buckets; off lo, hi, ci, 0
     uint32_t* hist;          // [ci][tpc][256]
+    uint32_t* bid;           // bucket of every element, one byte each (four per word)
     uint32_t* keys;          // bucket order: value bits
     uint32_t* vals;          // bucket order: position | bucket << 24
     uint32_t* keys2;         // ping-pong of the oversize-bucket sort
@@ -92,7 +103,6 @@ struct BkArgs {
     const float* s;          // sorted draws
     float* x_out;            // x[position] = s[rank]
     int tpc;
-    int stride;              // aux words per curve
     int gmax;
     uint32_t log2n;
 };
@@ -113,16 +123,17 @@ __device__ __forceinline__ uint32_t bucket_of(const float* spl, float v)
 }
 
 // ------------------------------------------------------------------ sample
-__global__ void __launch_bounds__(kBkThreads) k_bk_sample(const BkArgs a)
+__global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
 {
     const int ci = blockIdx.x;
+    if (ci == 0 && threadIdx.x == 0) *a.nitems = 0;  // before the scan kernel appends
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float sm[kBkSample];
     const int tid = threadIdx.x;
     const uint64_t off = a.curves[c].off;
     const uint32_t stride = (1u << a.log2n) / kBkSample;
-    for (int i = tid; i < kBkSample; i += kBkThreads) sm[i] = a.xadj[off + (uint64_t)i * stride + stride / 2];
+    for (int i = tid; i < kBkSample; i += kBkSampleThreads) sm[i] = a.xadj[off + (uint64_t)i * stride + stride / 2];
     __syncthreads();
     // bitonic sort, ascending; thread tid owns pair p = tid of every stage
     for (int k = 2; k <= kBkSample; k <<= 1) {
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_sample(const BkArgs a)
             __syncthreads();
         }
     }
-    uint32_t* A = a.aux + (size_t)ci * a.stride;
+    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
     if (tid < kBkBuckets - 1) A[kAuxSpl + tid] = __float_as_uint(sm[(kBkSample / kBkBuckets) * (tid + 1)]);
     if (tid == kBkBuckets - 1) A[kAuxSpl + tid] = 0x7f800000u;  // +inf, never compared
     if (tid == 0) {
@@ -148,6 +159,8 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_sample(const BkArgs a)
 }
 
 // ------------------------------------------------------------------ histogram
+// TPB tiles per block: bucket counts per tile, the bucket of every element
+// (one byte, packed four to a word, for the scatter), the tiles' min / max.
 template <int TPB>
 __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
 {
@@ -159,17 +172,16 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float spl[kBkBuckets];
-    __shared__ uint32_t h[TPB][W][kBkBuckets];
+    __shared__ uint32_t h[TPB][kBkBuckets];
     __shared__ uint32_t red[2][W];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t* A = a.aux + (size_t)ci * a.stride;
+    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
     spl[tid] = __uint_as_float(A[kAuxSpl + tid]);
 #pragma unroll
-    for (int u = 0; u < TPB; ++u)
-#pragma unroll
-        for (int w = 0; w < W; ++w) h[u][w][tid] = 0;
-    const uint64_t base = a.curves[c].off + (uint64_t)t0 * kSortTile;
-    const float4* __restrict__ src = (const float4*)(a.xadj + base);
+    for (int u = 0; u < TPB; ++u) h[u][tid] = 0;
+    const uint64_t off = a.curves[c].off;
+    const float4* __restrict__ src = (const float4*)(a.xadj + off + (uint64_t)t0 * kSortTile);
+    uint32_t* __restrict__ bid = a.bid + off + (uint64_t)t0 * (kSortTile / 4);
     float4 q[TPB * V4];
 #pragma unroll
     for (int e = 0; e < TPB * V4; ++e) {
@@ -180,15 +192,19 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
     uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
     for (int e = 0; e < TPB * V4; ++e) {
-        const int u = e / V4;
+        const int u = e / V4, v = tid + (e % V4) * kBkTileThreads;
         const float vv[4] = {q[e].x, q[e].y, q[e].z, q[e].w};
+        uint32_t word = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            atomicAdd(&h[u][warp][bucket_of(spl, vv[j])], 1u);
+            const uint32_t b = bucket_of(spl, vv[j]);
+            atomicAdd(&h[u][b], 1u);
+            word |= b << (8 * j);
             const uint32_t k = order_key(vv[j]);
             kmin = min(kmin, k);
             kmax = max(kmax, k);
         }
+        bid[(size_t)u * (kSortTile / 4) + v] = word;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -201,12 +217,7 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < TPB; ++u) {
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) cnt += h[u][w][tid];
-        a.hist[((size_t)ci * a.tpc + t0 + u) * kBkBuckets + tid] = cnt;
-    }
+    for (int u = 0; u < TPB; ++u) a.hist[((size_t)ci * a.tpc + t0 + u) * kBkBuckets + tid] = h[u][tid];
     if (tid == 0) {
         uint32_t m0 = red[0][0], m1 = red[1][0];
 #pragma unroll
@@ -228,6 +239,9 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
     if (!bk_active(a, c)) return;
     __shared__ uint32_t wsum[kBkBuckets / 32];
     __shared__ uint32_t cnt[kBkBuckets];
+    __shared__ uint32_t bs[kBkBuckets + 1];
+    __shared__ uint32_t gs[kBkBuckets + 1];
+    __shared__ uint32_t ng, first;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* h = a.hist + (size_t)ci * a.tpc * kBkBuckets + tid;
     uint32_t run = 0;
@@ -253,28 +267,55 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
     __syncthreads();
     uint32_t woff = 0;
     for (int w = 0; w < warp; ++w) woff += wsum[w];
-    uint32_t* A = a.aux + (size_t)ci * a.stride;
-    A[kAuxBase + tid] = woff + incl - run;
-    if (tid == kBkBuckets - 1) A[kAuxBase + kBkBuckets] = woff + incl;
+    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
+    const uint32_t base = woff + incl - run;
+    A[kAuxBase + tid] = base;
+    bs[tid] = base;
+    if (tid == kBkBuckets - 1) {
+        A[kAuxBase + kBkBuckets] = base + run;
+        bs[kBkBuckets] = base + run;
+    }
+    {
+        // the bucket's bounds and its sub-buckets per unit value (one
+        // sub-bucket per element, spread linearly over [lo, hi])
+        const float lo = tid == 0 ? key_value(A[kAuxMin]) : __uint_as_float(A[kAuxSpl + tid - 1]);
+        const float hi = tid == kBkBuckets - 1 ? key_value(A[kAuxMax]) : __uint_as_float(A[kAuxSpl + tid]);
+        const float d = hi - lo;
+        const float sc = (d > 0.0f && run > 0u) ? (float)run / d : 0.0f;
+        ((uint4*)(A + kAuxPar))[tid] = make_uint4(__float_as_uint(lo), __float_as_uint(sc), base, run);
+    }
     if (tid == 0) {
         // greedy groups of consecutive buckets holding at most kBkCap
         // elements; a larger bucket forms a group of its own
         uint32_t g = 0, acc = 0;
-        A[kAuxGstart] = 0;
+        gs[0] = 0;
         for (int b = 0; b < kBkBuckets; ++b) {
             const uint32_t n = cnt[b];
             if (acc > 0 && acc + n > (uint32_t)kBkCap) {
-                A[kAuxGstart + (++g)] = (uint32_t)b;
+                gs[++g] = (uint32_t)b;
                 acc = 0;
             }
             acc += n;
         }
-        A[kAuxGstart + g + 1] = kBkBuckets;
+        gs[g + 1] = kBkBuckets;
+        ng = g + 1;
         A[kAuxGcount] = g + 1;
+        first = atomicAdd(a.nitems, g + 1);
+    }
+    __syncthreads();
+    const uint64_t off = a.curves[c].off;
+    for (int g = tid; g < (int)ng; g += kBkBuckets) {
+        const uint32_t b0 = gs[g], b1 = gs[g + 1];
+        a.items[2 * (first + g)] = make_uint4(bs[b0], bs[b1] - bs[b0], b0, b1 - b0);
+        a.items[2 * (first + g) + 1] = make_uint4((uint32_t)off, (uint32_t)(off >> 32), (uint32_t)ci, 0u);
     }
 }
 
 // ------------------------------------------------------------------ scatter
+// One tile per block: its elements are placed in shared memory in bucket
+// order (slot atomics: the order inside a bucket is arbitrary), then each
+// bucket's run is written to the tile's slice of the bucket with coalesced
+// stores.
 __global__ void __launch_bounds__(kBkTileThreads) k_bk_scatter(const BkArgs a)
 {
     constexpr int V4 = kSortTile / 4 / kBkTileThreads;
@@ -282,38 +323,73 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_scatter(const BkArgs a)
     const int t = blockIdx.x % a.tpc;
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
-    __shared__ float spl[kBkBuckets];
+    __shared__ float stk[kSortTile];
+    __shared__ uint32_t stv[kSortTile];
     __shared__ uint32_t cur[kBkBuckets];
-    const int tid = threadIdx.x;
-    const uint32_t* A = a.aux + (size_t)ci * a.stride;
-    spl[tid] = __uint_as_float(A[kAuxSpl + tid]);
-    cur[tid] = a.hist[((size_t)ci * a.tpc + t) * kBkBuckets + tid] + A[kAuxBase + tid];
+    __shared__ uint32_t gb[kBkBuckets];
+    __shared__ uint32_t wsum[kBkTileThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
     const uint64_t off = a.curves[c].off;
     const uint32_t e0 = (uint32_t)t * kSortTile;
     const float4* __restrict__ src = (const float4*)(a.xadj + off + e0);
+    const uint32_t* __restrict__ bid = a.bid + off + e0 / 4;
     float4 q[V4];
+    uint32_t bw[V4];
 #pragma unroll
-    for (int e = 0; e < V4; ++e) q[e] = src[tid + e * kBkTileThreads];
+    for (int e = 0; e < V4; ++e) {
+        q[e] = src[tid + e * kBkTileThreads];
+        bw[e] = bid[tid + e * kBkTileThreads];
+    }
+    {
+        // the tile's count of bucket tid from the scanned tile prefixes
+        const uint32_t* hp = a.hist + ((size_t)ci * a.tpc + t) * kBkBuckets + tid;
+        const uint32_t pt = hp[0];
+        const uint32_t pn = t + 1 < a.tpc ? hp[kBkBuckets] : A[kAuxBase + tid + 1] - A[kAuxBase + tid];
+        const uint32_t n = pn - pt;
+        uint32_t incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t woff = 0;
+        for (int w = 0; w < warp; ++w) woff += wsum[w];
+        const uint32_t ls = woff + incl - n;   // the tile's first slot of bucket tid
+        cur[tid] = ls;
+        gb[tid] = A[kAuxBase + tid] + pt - ls;  // output index of slot i of bucket tid: gb + i
+    }
     __syncthreads();
-    uint32_t* __restrict__ kd = a.keys + off;
-    uint32_t* __restrict__ vd = a.vals + off;
 #pragma unroll
     for (int e = 0; e < V4; ++e) {
         const float vv[4] = {q[e].x, q[e].y, q[e].z, q[e].w};
         const uint32_t i0 = e0 + 4u * (uint32_t)(tid + e * kBkTileThreads);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const uint32_t b = bucket_of(spl, vv[j]);
-            const uint32_t pos = atomicAdd(&cur[b], 1u);
-            kd[pos] = __float_as_uint(vv[j]);
-            vd[pos] = (i0 + (uint32_t)j) | (b << 24);
+            const uint32_t b = (bw[e] >> (8 * j)) & 255u;
+            const uint32_t slot = atomicAdd(&cur[b], 1u);
+            stk[slot] = vv[j];
+            stv[slot] = (i0 + (uint32_t)j) | (b << 24);
         }
+    }
+    __syncthreads();
+    uint32_t* __restrict__ kd = a.keys + off;
+    uint32_t* __restrict__ vd = a.vals + off;
+#pragma unroll
+    for (int e = 0; e < kSortTile / kBkTileThreads; ++e) {
+        const int i = tid + e * kBkTileThreads;
+        const uint32_t v = stv[i];
+        const uint32_t dst = gb[v >> 24] + (uint32_t)i;
+        kd[dst] = __float_as_uint(stk[i]);
+        vd[dst] = v;
     }
 }
 
 // ------------------------------------------------------------------ finish
 // Block-wide exclusive scan of v (kBkThreads threads).
-__device__ __forceinline__ uint32_t bk_block_scan(uint32_t v, uint32_t* wsum, uint32_t* total)
+__device__ __forceinline__ uint32_t bk_block_scan(uint32_t v, uint32_t* wsum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t incl = v;
@@ -324,15 +400,10 @@ __device__ __forceinline__ uint32_t bk_block_scan(uint32_t v, uint32_t* wsum, ui
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    uint32_t woff = 0, tot = 0;
+    uint32_t woff = 0;
 #pragma unroll
-    for (int w = 0; w < kBkThreads / 32; ++w) {
-        const uint32_t x = wsum[w];
-        woff += w < warp ? x : 0u;
-        tot += x;
-    }
+    for (int w = 0; w < kBkThreads / 32; ++w) woff += w < warp ? wsum[w] : 0u;
     __syncthreads();
-    if (total) *total = tot;
     return woff + incl - v;
 }
 
@@ -350,13 +421,12 @@ __device__ bool bk_block_pass(const uint32_t* __restrict__ ik, const uint32_t* _
     auto digit = [&](uint32_t k, uint32_t v) -> uint32_t {
         return KEYB ? (order_key(__uint_as_float(k)) >> shift) & 255u : ((v & 0xffffffu) >> shift) & 255u;
     };
-    if (tid < 256) hist[tid] = 0;
+    hist[tid] = 0;  // kBkThreads == 256 digits
     __syncthreads();
     for (int i = tid; i < n; i += kBkThreads) atomicAdd(&hist[digit(ik[i], iv[i])], 1u);
     __syncthreads();
-    const bool one = tid < 256 && hist[tid] == (uint32_t)n;
-    if (__syncthreads_or(one)) return false;
-    uint32_t base = bk_block_scan(tid < 256 ? hist[tid] : 0u, wsum, nullptr);  // digit tid's base
+    if (__syncthreads_or(hist[tid] == (uint32_t)n)) return false;
+    uint32_t base = bk_block_scan(hist[tid], wsum);  // digit tid's first output index
     const uint32_t lt = (1u << lane) - 1u;
     for (int c0 = 0; c0 < n; c0 += kBkThreads) {
         for (int q = tid; q < W * 256; q += kBkThreads) (&wc[0][0])[q] = 0;
@@ -374,13 +444,11 @@ __device__ bool bk_block_pass(const uint32_t* __restrict__ ik, const uint32_t* _
         if (valid && below == 0) wc[warp][d] = __popc(peers);
         __syncthreads();
         uint32_t tot = 0;
-        if (tid < 256) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint32_t x = wc[w][tid];
-                wc[w][tid] = base + tot;
-                tot += x;
-            }
+        for (int w = 0; w < W; ++w) {
+            const uint32_t x = wc[w][tid];
+            wc[w][tid] = base + tot;
+            tot += x;
         }
         __syncthreads();
         if (valid) {
@@ -424,52 +492,59 @@ __device__ void bk_oversize(const BkArgs& a, uint64_t off, uint32_t e0, int n, u
     for (int r = threadIdx.x; r < n; r += kBkThreads) x[vf[r] & 0xffffffu] = s[r];
 }
 
-__global__ void __launch_bounds__(kBkThreads, 2) k_bk_finish(const BkArgs a)
+// Sub-buckets per element of a bucket (linear interpolation of the value
+// between the bucket's bounds): fewer elements share one, so fewer need the
+// comparison step.
+constexpr int kBkSubPer = 2;
+constexpr int kBkNsub = kBkSubPer * kBkCap;
+
+// Shared memory of the finish kernel (u32 words): values and positions |
+// sub-bucket << 17 in sub-bucket order, sub-bucket starts (nsub + 1),
+// cursors (then rank -> position), per-bucket parameters, scan partials.
+constexpr int kFinSk = 0;
+constexpr int kFinSi = kBkCap;
+constexpr int kFinSt = 2 * kBkCap;                  // kBkNsub + 1 (+3 pad)
+constexpr int kFinEn = kFinSt + kBkNsub + 4;        // cursors, then perm
+constexpr int kFinPar = kFinEn + kBkNsub;           // float2 lo/scale, uint2 first/count: 4 x 256
+constexpr int kFinWs = kFinPar + 4 * kBkBuckets;    // 8
+constexpr int kFinWords = kFinWs + 32;
+static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort scratch");
+static_assert(kBkMaxLog2 <= 17 && kBkNsub <= (1 << 15), "position | sub-bucket << 17 in one word");
+
+// One work item (a group of consecutive buckets of one curve) per block;
+// blocks past the items appended this iteration return at once.
+__global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
 {
-    const int ci = blockIdx.x / a.gmax;
-    const int g = blockIdx.x % a.gmax;
-    const int c = a.cls_curves[ci];
-    if (!bk_active(a, c)) return;
-    const uint32_t* A = a.aux + (size_t)ci * a.stride;
-    if ((uint32_t)g >= A[kAuxGcount]) return;
-    const uint32_t b0 = A[kAuxGstart + g], b1 = A[kAuxGstart + g + 1];
-    const uint32_t e0 = A[kAuxBase + b0], e1 = A[kAuxBase + b1];
-    const int n = (int)(e1 - e0);
+    constexpr uint32_t kPosMask = (1u << 17) - 1u;
+    const uint32_t item = blockIdx.x;
+    if (item >= *a.nitems) return;
+    const uint4 d0 = a.items[2 * item];
+    const uint4 d1 = a.items[2 * item + 1];
+    const uint32_t e0 = d0.x, b0 = d0.z;
+    const int n = (int)d0.y, nb = (int)d0.w;
     if (n == 0) return;
-    const uint64_t off = a.curves[c].off;
+    const uint64_t off = (uint64_t)d1.x | ((uint64_t)d1.y << 32);
+    const uint32_t* A = a.aux + (size_t)d1.z * kAuxCurveWords;
     extern __shared__ __align__(16) uint32_t bsm[];
     if (n > kBkCap) {  // one bucket of nearly equal values
         bk_oversize(a, off, e0, n, bsm);
         return;
     }
-    float* sk = (float*)bsm;                 // [kBkCap] values by sub-bucket
-    uint32_t* si = bsm + kBkCap;             // [kBkCap] positions by sub-bucket, then by rank
-    uint32_t* st = bsm + 2 * kBkCap;         // [kBkCap] sub-bucket counts, then starts
-    uint32_t* en = bsm + 3 * kBkCap;         // [kBkCap] sub-bucket cursors, then ends
-    float* plo = (float*)(bsm + 4 * kBkCap);           // [256] bucket lower bound
-    float* psc = (float*)(bsm + 4 * kBkCap + 256);     // [256] sub-buckets per unit value
-    uint32_t* poff = bsm + 4 * kBkCap + 512;           // [256] first sub-bucket of the bucket
-    uint32_t* pcnt = bsm + 4 * kBkCap + 768;           // [256] elements of the bucket
-    uint32_t* wsum = bsm + 4 * kBkCap + 1024;          // [16]
+    const int ns = kBkSubPer * n;  // sub-buckets of the group
+    float* sk = (float*)(bsm + kFinSk);
+    uint32_t* si = bsm + kFinSi;
+    uint32_t* st = bsm + kFinSt;
+    uint32_t* en = bsm + kFinEn;
+    float2* plo = (float2*)(bsm + kFinPar);                 // (lower bound, sub-buckets per unit)
+    uint2* pof = (uint2*)(bsm + kFinPar + 2 * kBkBuckets);  // (first sub-bucket, sub-buckets)
+    uint32_t* wsum = bsm + kFinWs;
     const int tid = threadIdx.x;
-    const int nb = (int)(b1 - b0);
-    for (int i = tid; i < nb; i += kBkThreads) {
-        const uint32_t b = b0 + (uint32_t)i;
-        const float lo = b == 0 ? key_value(A[kAuxMin]) : __uint_as_float(A[kAuxSpl + b - 1]);
-        const float hi = b == kBkBuckets - 1 ? key_value(A[kAuxMax]) : __uint_as_float(A[kAuxSpl + b]);
-        const uint32_t cb = A[kAuxBase + b + 1] - A[kAuxBase + b];
-        const float d = hi - lo;
-        plo[i] = lo;
-        psc[i] = (d > 0.0f && cb > 0u) ? (float)cb / d : 0.0f;
-        poff[i] = A[kAuxBase + b] - e0;
-        pcnt[i] = cb;
-    }
-    for (int i = tid; i < kBkCap; i += kBkThreads) st[i] = 0u;
-    __syncthreads();
-    // load; sub-bucket of every element (monotone in the value inside a bucket)
+    // every global load of the block in flight first: the group's values and
+    // positions, the sorted draws of its ranks, the buckets' parameters
     const uint32_t* __restrict__ kin = a.keys + off + e0;
     const uint32_t* __restrict__ vin = a.vals + off + e0;
-    float key[kBkPer];
+    const float* __restrict__ s = a.s + off + e0;
+    float key[kBkPer], sv[kBkPer];
     uint32_t pos[kBkPer], sub[kBkPer];
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
@@ -477,89 +552,111 @@ __global__ void __launch_bounds__(kBkThreads, 2) k_bk_finish(const BkArgs a)
         if (p < n) {
             key[j] = __uint_as_float(kin[p]);
             pos[j] = vin[p];
+            sv[j] = s[p];
         }
     }
+    static_assert(kBkThreads >= kBkBuckets, "one thread per bucket of a group");
+    if (tid < nb) {
+        const uint4 P = ((const uint4*)(A + kAuxPar))[b0 + (uint32_t)tid];
+        // P.y: elements per unit value; kBkSubPer sub-buckets per element
+        plo[tid] = make_float2(__uint_as_float(P.x), (float)kBkSubPer * __uint_as_float(P.y));
+        pof[tid] = make_uint2((uint32_t)kBkSubPer * (P.z - e0), (uint32_t)kBkSubPer * P.w);
+    }
+    for (int i = tid; i <= ns; i += kBkThreads) st[i] = 0u;
+    __syncthreads();
+    // sub-bucket of every element (kBkSubPer per element of its bucket, by
+    // linear interpolation between the bucket's bounds: monotone in the value)
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
         const int p = tid + j * kBkThreads;
         if (p < n) {
             const uint32_t bl = min((pos[j] >> 24) - b0, (uint32_t)nb - 1u);
-            pos[j] &= 0xffffffu;
-            const float f = (key[j] - plo[bl]) * psc[bl];
-            int sb = __float2int_rz(f);  // NaN -> 0
-            sb = max(0, min(sb, (int)pcnt[bl] - 1));
-            sub[j] = poff[bl] + (uint32_t)sb;
+            pos[j] &= kPosMask;
+            const float2 ls = plo[bl];
+            const uint2 of = pof[bl];
+            int q = __float2int_rz((key[j] - ls.x) * ls.y);  // NaN -> 0
+            q = max(0, min(q, (int)of.y - 1));
+            sub[j] = of.x + (uint32_t)q;
             atomicAdd(&st[sub[j]], 1u);
         }
     }
     __syncthreads();
-    // exclusive scan of the n sub-bucket counts: thread tid owns kBkPer consecutive ones
+    // exclusive scan of the ns sub-bucket counts (thread tid owns the
+    // consecutive ones from kSc tid); cursors = starts
     {
-        uint32_t v[kBkPer], sum = 0;
+        constexpr int kSc = kBkNsub / kBkThreads;  // 16
+        static_assert(kSc % 4 == 0, "16-byte loads");
+        uint32_t cn[kSc];
+        const int q0 = tid * kSc;
 #pragma unroll
-        for (int j = 0; j < kBkPer; ++j) {
-            const int q = tid * kBkPer + j;
-            v[j] = q < n ? st[q] : 0u;
-            sum += v[j];
+        for (int j = 0; j < kSc; j += 4) {
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (q0 + j < ns) v = *(const uint4*)(st + q0 + j);  // words to ns + 3: zeroed or counted
+            cn[j] = v.x; cn[j + 1] = v.y; cn[j + 2] = v.z; cn[j + 3] = v.w;
         }
-        uint32_t run = bk_block_scan(sum, wsum, nullptr);
+        uint32_t sum = 0;
 #pragma unroll
-        for (int j = 0; j < kBkPer; ++j) {
-            const int q = tid * kBkPer + j;
-            if (q < n) {
-                st[q] = run;
-                en[q] = run;
+        for (int j = 0; j < kSc; ++j) sum += q0 + j < ns ? cn[j] : 0u;
+        uint32_t run = bk_block_scan(sum, wsum);
+#pragma unroll
+        for (int j = 0; j < kSc; j += 4) {
+            uint32_t o[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                o[t] = run;
+                run += q0 + j + t < ns ? cn[j + t] : 0u;
             }
-            run += v[j];
+            if (q0 + j < ns) {
+                *(uint4*)(st + q0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
+                *(uint4*)(en + q0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
         }
     }
     __syncthreads();
+    if (tid == 0) st[ns] = (uint32_t)n;
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
         const int p = tid + j * kBkThreads;
         if (p < n) {
             const uint32_t q = atomicAdd(&en[sub[j]], 1u);
             sk[q] = key[j];
-            si[q] = pos[j];
+            si[q] = pos[j] | (sub[j] << 17);
         }
     }
     __syncthreads();
-    // rank among the sub-bucket's members by (value, position)
-    uint32_t lr[kBkPer];
+    // rank in sub-bucket order (the placement left each sub-bucket unordered):
+    // r = start + members with a smaller (value, position); neighbouring
+    // lanes hold neighbouring sub-buckets; en becomes rank -> position
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
-        const int p = tid + j * kBkThreads;
-        if (p < n) {
-            const uint32_t s0 = st[sub[j]], s1 = en[sub[j]];
-            uint32_t r = s0;
-            for (uint32_t q = s0; q < s1; ++q) {
-                const float kq = sk[q];
-                r += (kq < key[j] || (kq == key[j] && si[q] < pos[j])) ? 1u : 0u;
+        const int q = tid + j * kBkThreads;
+        if (q < n) {
+            const uint32_t w = si[q];
+            const uint32_t u = w >> 17, p = w & kPosMask;
+            const uint32_t s0 = st[u], s1 = st[u + 1];
+            uint32_t r = (uint32_t)q;
+            if (s1 - s0 > 1u) {
+                const float k = sk[q];
+                r = s0;
+                for (uint32_t m = s0; m < s1; ++m) {
+                    const float km = sk[m];
+                    const uint32_t pm = si[m] & kPosMask;
+                    r += (km < k || (km == k && pm < p)) ? 1u : 0u;
+                }
             }
-            lr[j] = r;
+            en[r] = p;
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kBkPer; ++j)
-        if (tid + j * kBkThreads < n) si[lr[j]] = pos[j];
-    __syncthreads();
-    const float* __restrict__ s = a.s + off + e0;
     float* __restrict__ x = a.x_out + off;
-    float sv[kBkPer];
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
         const int r = tid + j * kBkThreads;
-        if (r < n) sv[j] = s[r];
-    }
-#pragma unroll
-    for (int j = 0; j < kBkPer; ++j) {
-        const int r = tid + j * kBkThreads;
-        if (r < n) x[si[r]] = sv[j];
+        if (r < n) x[en[r]] = sv[j];
     }
 }
 
-constexpr size_t kBkFinishSmem = (size_t)(4 * kBkCap + 1024 + 32) * 4;
+constexpr size_t kBkFinishSmem = (size_t)kFinWords * 4;
 
 cudaError_t bucket_kernel_attributes()
 {
@@ -575,8 +672,11 @@ void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, v
     a.eff_iters = p.d_eff_iters;
     a.d_iter = gated ? p.d_iter : nullptr;
     a.xadj = (const float*)src;
-    a.aux = k.d_aux;
+    a.nitems = k.d_aux;
+    a.aux = k.d_aux + kAuxHeader;
+    a.items = (uint4*)(k.d_aux + kAuxHeader + (size_t)k.ncurves * kAuxCurveWords);
     a.hist = p.d_hist + k.hist_off;
+    a.bid = p.d_valsB;  // free until the finish: the bucket bytes of curve c at word off_c
     a.keys = (uint32_t*)p.d_keysA;
     a.vals = p.d_valsA;
     a.keys2 = (uint32_t*)p.d_f;
@@ -584,11 +684,10 @@ void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, v
     a.s = (const float*)p.d_s;
     a.x_out = (float*)(x_out ? x_out : p.d_x);
     a.tpc = k.tiles_per_curve;
-    a.stride = (int)bucket_aux_words(k.log2n);
     a.gmax = bucket_gmax(k.log2n);
     a.log2n = k.log2n;
     if (kt) kt->begin(kGroupSortHistScan, st);
-    k_bk_sample<<<k.ncurves, kBkThreads, 0, st>>>(a);
+    k_bk_sample<<<k.ncurves, kBkSampleThreads, 0, st>>>(a);
     const int tpb = std::min(4, a.tpc);
     if (tpb >= 4) k_bk_hist<4><<<k.ncurves * (a.tpc / 4), kBkTileThreads, 0, st>>>(a);
     else if (tpb >= 2) k_bk_hist<2><<<k.ncurves * (a.tpc / 2), kBkTileThreads, 0, st>>>(a);
@@ -597,7 +696,7 @@ void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, v
     if (kt) kt->end(st);
     if (kt) kt->begin(kGroupSortScatter, st);
     k_bk_scatter<<<k.ncurves * a.tpc, kBkTileThreads, 0, st>>>(a);
-    k_bk_finish<<<k.ncurves * a.gmax, kBkThreads, kBkFinishSmem, st>>>(a);
+    k_bk_finish<<<(unsigned)(k.ncurves * a.gmax), kBkThreads, kBkFinishSmem, st>>>(a);
     if (kt) kt->end(st);
     if (launches) *launches += 5;
 }

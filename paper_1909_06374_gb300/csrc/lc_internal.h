@@ -31,7 +31,7 @@ struct ClassInfo {
     bool resident = false;             // iterated by the fused on-chip kernel
     float* d_rx = nullptr;             // L2 exchange area of the cluster kernel (3 N floats per curve)
     bool bucket = false;               // argsort by the sample sort of lc_bucket.cu
-    uint32_t* d_aux = nullptr;         // its per-curve splitters, bases and groups
+    uint32_t* d_aux = nullptr;         // its splitters, bases and work items
     int ntab = 0;                      // curves with a tabulated ERDF (Eq. 1 smooth, Eq. 2)
     int* d_tab_curves = nullptr;       // their curve indices (device)
     std::vector<int> h_tab_curves;
@@ -178,16 +178,16 @@ template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const 
                                        bool gated, cudaStream_t st, uint64_t* launches, void* x_out = nullptr,
                                        KernelTimes* kt = nullptr);
 // sample-sort argsort of the iteration (lc_bucket.cu): FP32 curves of
-// 2^kBkMinLog2 .. 2^kBkMaxLog2 samples; groups of at most kBkCap elements are
-// ranked in shared memory
-constexpr int kBkCap = 4096;
+// 2^kBkMinLog2 .. 2^kBkMaxLog2 samples (256 buckets of N/256 elements on
+// average); groups of at most kBkCap elements are ranked in shared memory
+constexpr int kBkCap = 2048;
 constexpr uint32_t kBkMinLog2 = 13;
-constexpr uint32_t kBkMaxLog2 = 18;
+constexpr uint32_t kBkMaxLog2 = 17;
 bool bucket_supported(lc_precision prec, uint32_t log2n);
 // LC_SORT=radix keeps the LSD radix argsort for every length
 bool bucket_enabled_from_env();
 int bucket_gmax(uint32_t log2n);
-size_t bucket_aux_words(uint32_t log2n);  // u32 words per curve
+size_t bucket_aux_words(uint32_t log2n, int ncurves);  // u32 words of a class
 cudaError_t bucket_kernel_attributes();
 // x_out[perm[r]] = s[r] with perm the stable argsort of `src` (gated).
 void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, void* x_out, bool gated,

@@ -127,7 +127,7 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
     k.d_curves = (int*)take(sizeof(int));
     if (resident_exchange_floats(k.log2n)) k.d_rx = (float*)take(resident_exchange_floats(k.log2n) * 4);
     k.bucket = bucket_enabled_from_env() && bucket_supported(LC_FP32, k.log2n);
-    if (k.bucket) k.d_aux = (uint32_t*)take(bucket_aux_words(k.log2n) * 4);
+    if (k.bucket) k.d_aux = (uint32_t*)take(bucket_aux_words(k.log2n, 1) * 4);
     if (tabulated) {
         // the CDF table of a smooth (Eq. 1) or log-normal (Eq. 2) ERDF
         p.ntab = 1;
