@@ -328,30 +328,58 @@ LC_API lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* strea
 
 /* ---------------------------------------------------------------- serving */
 
-/* A continuous-batching server on `device`: jobs submitted at any time are
- * admitted while their device footprint fits in hbm_budget_bytes, run in
- * batched iteration steps alongside the other active jobs, and retired when
- * their iteration count is reached.  A host thread owned by the server drives
- * the device.  hbm_budget_bytes = 0 uses 80 % of the free device memory. */
+/* A continuous-batching server on `device` (the serving form of Sec. 2.1's
+ * generator): jobs submitted at any time are admitted as soon as a slot of
+ * the server's device buffers is free for them, run in batched iteration
+ * steps alongside the other active jobs, and retired when their iteration
+ * count is reached; a retired job's slot is free for the next job at once.
+ * At creation the server allocates buffers ("planes") of a power-of-two
+ * capacity of C samples in 7/8 of hbm_budget_bytes (state, FFT, draws, sort
+ * keys and positions, amplitudes, TK spectrum: about 40 bytes per sample in
+ * FP32); every job takes a slot of 2^max(log2n, 4) samples.  Jobs are
+ * admitted in arrival order, skipping one whose slot cannot be allocated yet
+ * unless it has waited for more than a second, after which no later job is
+ * admitted before it.  A host thread owned by the server drives the device.
+ * hbm_budget_bytes = 0 uses 80 % of the free device memory; LC_ERR_INVALID if
+ * the budget holds no slot of 16 samples, LC_ERR_NOMEM if the planes cannot
+ * be allocated. */
 LC_API lc_status lc_server_create(int device, size_t hbm_budget_bytes, lc_precision prec,
                            lc_server* out);
 
 /* Queue one job (copied; non-blocking).  LC_ERR_BUSY if the queue is full,
- * LC_ERR_INVALID for a bad job. */
+ * LC_ERR_INVALID for a bad job or one longer than the server's capacity. */
 LC_API lc_status lc_submit(lc_server server, const lc_job* job, lc_ticket* out);
 
 /* Non-blocking completion check.  LC_PENDING while the job runs; LC_OK when
  * it has finished, after copying its N results into out (host pointer) and
  * the submit-to-finish latency into *latency_ns (either may be NULL); the
- * ticket is then released.  LC_ERR_UNKNOWN_TICKET otherwise. */
+ * ticket is then released.  A job whose cohort failed returns that error
+ * once (LC_ERR_NOMEM when its cohort's tables could not be allocated with no
+ * other cohort running, LC_ERR_CUDA otherwise) and the server keeps serving;
+ * LC_ERR_CUDA for every ticket only after an error that leaves the CUDA
+ * context unusable.  LC_ERR_UNKNOWN_TICKET otherwise. */
 LC_API lc_status lc_poll(lc_server server, lc_ticket ticket, void* out_host, uint64_t* latency_ns);
 
 /* Jobs finished, jobs active on the device, jobs waiting for admission. */
 LC_API lc_status lc_server_stats(lc_server server, uint64_t* finished, uint64_t* active,
                           uint64_t* waiting);
 
+/* Device-time record of the server's chunks (CUDA events on the cohorts'
+ * streams, up to 65536 chunks): *busy_ms = time with at least one chunk on
+ * the device, *overlap_ms = time with chunks of two or more cohorts running
+ * at once; *free_samples / *capacity = free and total samples of the planes.
+ * Any pointer may be NULL. */
+LC_API lc_status lc_server_trace(lc_server server, double* busy_ms, double* overlap_ms, uint64_t* free_samples,
+                                 uint64_t* capacity);
+
 /* Stop the server thread, drop unfinished jobs and free its memory. */
 LC_API lc_status lc_server_destroy(lc_server server);
+
+/* Device bytes that lc_plan_create allocates for these jobs (the value
+ * lc_plan_workspace_bytes then reports), computed on the host from the same
+ * layout without any device call.  LC_ERR_INVALID as lc_plan_create for bad
+ * jobs. */
+LC_API lc_status lc_plan_footprint(const lc_job* jobs, size_t njobs, lc_precision prec, size_t* bytes);
 
 #ifdef __cplusplus
 }

@@ -13,15 +13,16 @@ from ._abi import (LC_FP32, LC_FP64, LcError, lc_generate, lc_generate_host, lc_
                    lc_periodogram, lc_plan_buffer, lc_plan_convergence, lc_plan_create, lc_plan_destroy,
                    lc_plan_last_launches, lc_plan_profile, lc_structure_function,
                    lc_plan_set_convergence, lc_plan_timing, lc_plan_total_samples, lc_plan_workspace_bytes,
-                   lc_poll, lc_rank_replace, lc_server_create, lc_server_destroy, lc_server_stats,
-                   lc_set_state, lc_setup, lc_submit)
+                   lc_plan_footprint, lc_poll, lc_rank_replace, lc_server_create, lc_server_destroy,
+                   lc_server_stats, lc_server_trace, lc_set_state, lc_setup, lc_submit)
 
 __all__ = ["Plan", "LC_FP32", "LC_FP64", "LcError", "lc_plan_create", "lc_generate", "lc_generate_host",
            "lc_setup", "lc_iterate", "lc_get_state", "lc_set_state", "lc_rank_replace", "lc_plan_buffer",
            "lc_plan_last_launches", "lc_plan_timing", "lc_plan_total_samples", "lc_plan_workspace_bytes", "lc_plan_destroy",
            "lc_plan_set_convergence", "lc_plan_convergence", "lc_periodogram", "lc_structure_function",
            "lc_plan_profile",
-           "lc_server_create", "lc_submit", "lc_poll", "lc_server_stats", "lc_server_destroy"]
+           "lc_plan_footprint",
+           "lc_server_create", "lc_submit", "lc_poll", "lc_server_stats", "lc_server_trace", "lc_server_destroy"]
 
 
 class Plan:

@@ -78,6 +78,9 @@ _SIGS = {
     "lc_poll": (c_i32, [c_p, c_u64, c_p, ctypes.POINTER(c_u64)]),
     "lc_server_stats": (c_i32, [c_p, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)]),
     "lc_server_destroy": (c_i32, [c_p]),
+    "lc_server_trace": (c_i32, [c_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)]),
+    "lc_plan_footprint": (c_i32, [ctypes.POINTER(LcJob), c_sz, c_i32, ctypes.POINTER(c_sz)]),
 }
 
 _lock = threading.Lock()
@@ -309,3 +312,19 @@ def lc_server_stats(server):
 
 def lc_server_destroy(server):
     _check(load().lc_server_destroy(server), "lc_server_destroy")
+
+
+def lc_server_trace(server):
+    """dict(busy_ms, overlap_ms, free_samples, capacity) of a server (see agnlc.h)."""
+    b, o, f, c = ctypes.c_double(), ctypes.c_double(), c_u64(), c_u64()
+    _check(load().lc_server_trace(server, ctypes.byref(b), ctypes.byref(o), ctypes.byref(f), ctypes.byref(c)),
+           "lc_server_trace")
+    return {"busy_ms": b.value, "overlap_ms": o.value, "free_samples": f.value, "capacity": c.value}
+
+
+def lc_plan_footprint(jobs, prec=LC_FP32):
+    """Device bytes lc_plan_create would allocate for these jobs (host only)."""
+    arr = job_array(jobs)
+    n = c_sz()
+    _check(load().lc_plan_footprint(arr, len(jobs), int(prec), ctypes.byref(n)), "lc_plan_footprint")
+    return n.value

@@ -111,8 +111,6 @@ CurveDev curve_from_job(const lc_job& j)
     return cv;
 }
 
-static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
 int path_mode_from_env()
 {
     const char* e = std::getenv("LC_PATH");
@@ -132,35 +130,19 @@ int resident_max_log2_from_env()
     return (int)v;
 }
 
-template <typename T>
-static lc_status build_tables(Plan& p)
+// Everything of a plan that needs no device: validation, curve descriptors
+// and offsets (in job order, or at the given external offsets), classes and
+// their per-class sizes.
+static lc_status plan_describe(const lc_job* jobs, size_t njobs, lc_precision prec, const uint64_t* ext_off,
+                               Plan& P)
 {
-    for (auto& k : p.classes) launch_twiddles<T>(k, p.stream);
-    LC_CK(cudaGetLastError());
-    return LC_OK;
-}
-
-lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device, Plan** out)
-{
-    if (!jobs || njobs == 0 || !out) { set_error("null jobs / out or njobs == 0"); return LC_ERR_INVALID; }
+    if (!jobs || njobs == 0) { set_error("null jobs or njobs == 0"); return LC_ERR_INVALID; }
     if (prec != LC_FP32 && prec != LC_FP64) { set_error("bad precision"); return LC_ERR_INVALID; }
     for (size_t i = 0; i < njobs; ++i) {
         lc_status s = validate_job(jobs[i]);
         if (s != LC_OK) { set_error("job " + std::to_string(i) + ": " + g_last_error); return s; }
     }
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
-        cudaGetLastError();
-        set_error("no such CUDA device"); return LC_ERR_INVALID;
-    }
-    DeviceGuard g(device);
-    {
-        const lc_status ps = prepare_kernels(device);
-        if (ps != LC_OK) return ps;
-    }
-    Plan* p = new (std::nothrow) Plan();
-    if (!p) return LC_ERR_NOMEM;
-    p->device = device;
+    Plan* p = &P;
     p->prec = prec;
     p->ncurves = njobs;
     // Path selection (a tuning knob; results depend only on length,
@@ -172,8 +154,6 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->path_mode = path_mode_from_env();
     p->res_max_log2 = resident_max_log2_from_env();
     p->jobs.assign(jobs, jobs + njobs);
-    const size_t ts = prec == LC_FP32 ? 4 : 8;
-
     // curves in job order; classes by length
     p->h_curves.resize(njobs);
     size_t off = 0, offh = 0;
@@ -182,7 +162,13 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         const lc_job& j = jobs[c];
         CurveDev& cv = p->h_curves[c];
         cv = curve_from_job(j);
-        cv.off = off; cv.offh = offh;
+        if (ext_off) {
+            cv.off = ext_off[c];
+            cv.offh = ext_half_offset(cv.off);
+        } else {
+            cv.off = off;
+            cv.offh = offh;
+        }
         if (cls_of_len[j.log2n] < 0) {
             cls_of_len[j.log2n] = (int)p->classes.size();
             p->classes.emplace_back();
@@ -201,84 +187,189 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     }
     p->total = off;
     p->total_h = offh;
-
     for (auto& k : p->classes) {
         if (k.log2n - 1 >= 12 && !tile_schedule_ok(k.log2n - 1, prec == LC_FP64)) {
             set_error("internal: no tile schedule for log2n = " + std::to_string(k.log2n));
-            delete p;
             return LC_ERR_INVALID;
         }
     }
-    // arena layout
-    size_t hist = 0, cbase = 0, partial = 0, twb = 0, rxb = 0, auxb = 0;
     const bool bucket_on = bucket_enabled_from_env();
     for (auto& k : p->classes) {
         k.ncurves = (int)k.h_curves.size();
         k.bucket = bucket_on && bucket_supported(prec, k.log2n);
-        if (k.bucket) auxb += align_up(bucket_aux_words(k.log2n, k.ncurves) * 4, 256);
         k.radices = fft_radices(k.log2n - 1);
         const size_t n = 1ull << k.log2n;
         k.tile_len = (int)std::min<size_t>(n, kSortTile);
         k.tiles_per_curve = (int)(n / k.tile_len);
         k.nchunks = (k.tiles_per_curve + kScanChunk - 1) / kScanChunk;
+        k.resident = resident_supported(*p, k.log2n);
+    }
+    return LC_OK;
+}
+
+// Byte offsets of a plan's device arena.  With external planes the state,
+// FFT, amplitude, draw and sort buffers live there instead (at the curves'
+// own offsets) and the arena holds only the per-plan tables.
+struct PlanLayout {
+    size_t bytes = 0;
+    size_t curves, erdf, sigma, eff, iter, partial, x, f, A, s, sort, hist, cbase, tw, cls, lags, tabc, tab, rx, aux;
+    size_t nhist = 0, ncbase = 0, npartial = 0;
+};
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static PlanLayout plan_layout(Plan& P, bool ext)
+{
+    Plan* p = &P;
+    const size_t ts = p->prec == LC_FP32 ? 4 : 8;
+    const size_t njobs = p->ncurves;
+    PlanLayout L;
+    size_t hist = 0, cbase = 0, partial = 0, twb = 0, rxb = 0, auxb = 0;
+    for (auto& k : p->classes) {
+        const size_t n = 1ull << k.log2n;
+        if (k.bucket) auxb += align_up(bucket_aux_words(k.log2n, k.ncurves) * 4, 256);
         k.hist_off = hist;  hist += (size_t)k.ncurves * k.tiles_per_curve * 256;
         k.cbase_off = cbase; cbase += (size_t)k.ncurves * k.nchunks * 256;
         k.partial_off = partial; partial += (size_t)k.ncurves * spec_blocks_per_curve(k.log2n);
         twb += align_up((n / 2) * 2 * ts, 256);
         rxb += align_up((size_t)k.ncurves * resident_exchange_floats(k.log2n) * 4, 256);
     }
-    const size_t A256 = 256;
+    L.nhist = hist; L.ncbase = cbase; L.npartial = partial;
     size_t sz = 0;
-    auto take = [&](size_t bytes) { size_t o = sz; sz = align_up(sz + bytes, A256); return o; };
-    const size_t o_curves = take(sizeof(CurveDev) * njobs);
-    const size_t o_erdf = take(sizeof(ErdfConst) * njobs);
-    const size_t o_sigma = take(sizeof(double) * 2 * njobs);  // realised, then PSD
-    const size_t o_eff = take(sizeof(uint32_t) * njobs);
-    const size_t o_iter = take(sizeof(int) * 4);
-    const size_t o_partial = take(sizeof(double) * 2 * partial);
-    const size_t o_x = take(p->total * ts);
-    const size_t o_f = take(p->total * ts);
-    const size_t o_A = take(p->total_h * ts);
-    const size_t o_s = take(p->total * ts);
-    const size_t sortbytes = std::max(2 * p->total * ts + 2 * p->total * 4, 16 * p->total_h);
-    const size_t o_sort = take(sortbytes);
-    const size_t o_hist = take(sizeof(uint32_t) * hist);
-    const size_t o_cbase = take(sizeof(uint32_t) * cbase);
-    const size_t o_tw = take(twb);
-    const size_t o_cls = take(sizeof(int) * njobs);
-    const size_t o_lags = take(sizeof(uint32_t) * kMaxLags);
-    const size_t o_tabc = take(sizeof(int) * 2 * p->ntab);  // all, then per class
-    const size_t o_tab = take(sizeof(double) * (kErdfTable + 1) * p->ntab);
-    const size_t o_rx = prec == LC_FP32 ? take(rxb) : 0;
-    const size_t o_aux = take(auxb);
-    p->arena_bytes = sz;
-    if (cudaMalloc(&p->arena, sz) != cudaSuccess) {
+    auto take = [&](size_t bytes) { size_t o = sz; sz = align_up(sz + bytes, 256); return o; };
+    L.curves = take(sizeof(CurveDev) * njobs);
+    L.erdf = take(sizeof(ErdfConst) * njobs);
+    L.sigma = take(sizeof(double) * 2 * njobs);  // realised, then PSD
+    L.eff = take(sizeof(uint32_t) * njobs);
+    L.iter = take(sizeof(int) * 4);
+    L.partial = take(sizeof(double) * 2 * partial);
+    if (!ext) {
+        L.x = take(p->total * ts);
+        L.f = take(p->total * ts);
+        L.A = take(p->total_h * ts);
+        L.s = take(p->total * ts);
+        L.sort = take(std::max(2 * p->total * ts + 2 * p->total * 4, 16 * p->total_h));
+    } else {
+        L.x = L.f = L.A = L.s = L.sort = 0;
+    }
+    L.hist = take(sizeof(uint32_t) * hist);
+    L.cbase = take(sizeof(uint32_t) * cbase);
+    L.tw = take(twb);
+    L.cls = take(sizeof(int) * njobs);
+    L.lags = take(sizeof(uint32_t) * kMaxLags);
+    L.tabc = take(sizeof(int) * 2 * p->ntab);  // all, then per class
+    L.tab = take(sizeof(double) * (kErdfTable + 1) * p->ntab);
+    L.rx = p->prec == LC_FP32 ? take(rxb) : 0;
+    L.aux = take(auxb);
+    L.bytes = sz;
+    return L;
+}
+
+size_t ext_half_offset(uint64_t off) { return (size_t)(off / 2 + off / 16); }
+
+size_t ext_plane_bytes_per_sample(lc_precision prec)
+{
+    const size_t ts = prec == LC_FP32 ? 4 : 8;
+    // x, f, s, two key and two position planes; amplitudes and the FP64 TK
+    // spectrum at the half offsets (9/16 of an entry per sample)
+    return 5 * ts + 2 * 4 + (ts * 9 + 15) / 16 + 9;
+}
+
+lc_status plan_arena_bytes(const lc_job* jobs, size_t njobs, lc_precision prec, bool ext, size_t* bytes)
+{
+    Plan p;
+    std::vector<uint64_t> offs;
+    if (ext) {
+        uint64_t o = 0;
+        for (size_t i = 0; i < njobs; ++i) { offs.push_back(o); o += 1ull << (jobs ? jobs[i].log2n : 0); }
+    }
+    lc_status st = plan_describe(jobs, njobs, prec, ext ? offs.data() : nullptr, p);
+    if (st != LC_OK) return st;
+    *bytes = plan_layout(p, ext).bytes;
+    return LC_OK;
+}
+
+template <typename T>
+static lc_status build_tables(Plan& p)
+{
+    for (auto& k : p.classes) launch_twiddles<T>(k, p.stream);
+    LC_CK(cudaGetLastError());
+    return LC_OK;
+}
+
+lc_status plan_create_ext(const lc_job* jobs, size_t njobs, lc_precision prec, int device, const ExtPlanes* ext,
+                          const uint64_t* ext_off, Plan** out)
+{
+    if (!out) { set_error("out is null"); return LC_ERR_INVALID; }
+    if (ext && !ext_off) { set_error("external planes need the curves' offsets"); return LC_ERR_INVALID; }
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) return LC_ERR_NOMEM;
+    {
+        const lc_status ds = plan_describe(jobs, njobs, prec, ext ? ext_off : nullptr, *p);
+        if (ds != LC_OK) { delete p; return ds; }
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
-        set_error("device allocation of " + std::to_string(sz) + " bytes failed");
+        delete p;
+        set_error("no such CUDA device"); return LC_ERR_INVALID;
+    }
+    DeviceGuard g(device);
+    {
+        const lc_status ps = prepare_kernels(device);
+        if (ps != LC_OK) { delete p; return ps; }
+    }
+    p->device = device;
+    p->ext = ext != nullptr;
+    const size_t ts = prec == LC_FP32 ? 4 : 8;
+    const PlanLayout L = plan_layout(*p, p->ext);
+    p->arena_bytes = L.bytes;
+    p->partial_total = L.npartial;
+    cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { set_error(std::string("stream: ") + cudaGetErrorString(e)); delete p; return LC_ERR_CUDA; }
+    // with external planes the arena is stream-ordered (no device-wide
+    // synchronisation when a server starts or ends a cohort)
+    e = p->ext ? cudaMallocAsync(&p->arena, L.bytes, p->stream) : cudaMalloc(&p->arena, L.bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of " + std::to_string(L.bytes) + " bytes failed");
+        cudaStreamDestroy(p->stream);
         delete p;
         return LC_ERR_NOMEM;
     }
     char* base = (char*)p->arena;
-    p->d_curves = (CurveDev*)(base + o_curves);
-    p->d_erdf = (ErdfConst*)(base + o_erdf);
-    p->d_sigma = (double*)(base + o_sigma);
-    p->d_eff_iters = (uint32_t*)(base + o_eff);
-    p->d_iter = (int*)(base + o_iter);
-    p->d_partial = (double*)(base + o_partial);
-    p->d_lags = (uint32_t*)(base + o_lags);
-    p->partial_total = partial;
-    p->d_x = base + o_x;
-    p->d_f = base + o_f;
-    p->d_A = base + o_A;
-    p->d_s = base + o_s;
-    p->d_keysA = base + o_sort;
-    p->d_keysB = base + o_sort + p->total * ts;
-    p->d_valsA = (uint32_t*)(base + o_sort + 2 * p->total * ts);
-    p->d_valsB = (uint32_t*)(base + o_sort + 2 * p->total * ts + p->total * 4);
-    p->d_spec = (double2*)(base + o_sort);
-    p->d_hist = (uint32_t*)(base + o_hist);
-    p->d_cbase = (uint32_t*)(base + o_cbase);
-    size_t tw_at = o_tw, cls_at = o_cls, rx_at = o_rx, aux_at = o_aux;
+    p->d_curves = (CurveDev*)(base + L.curves);
+    p->d_erdf = (ErdfConst*)(base + L.erdf);
+    p->d_sigma = (double*)(base + L.sigma);
+    p->d_eff_iters = (uint32_t*)(base + L.eff);
+    p->d_iter = (int*)(base + L.iter);
+    p->d_partial = (double*)(base + L.partial);
+    p->d_lags = (uint32_t*)(base + L.lags);
+    if (p->ext) {
+        p->d_x = ext->x;
+        p->d_f = ext->f;
+        p->d_A = ext->A;
+        p->d_s = ext->s;
+        p->d_keysA = ext->keysA;
+        p->d_keysB = ext->keysB;
+        p->d_valsA = ext->valsA;
+        p->d_valsB = ext->valsB;
+        p->d_spec = ext->spec;
+    } else {
+        p->d_x = base + L.x;
+        p->d_f = base + L.f;
+        p->d_A = base + L.A;
+        p->d_s = base + L.s;
+        p->d_keysA = base + L.sort;
+        p->d_keysB = base + L.sort + p->total * ts;
+        p->d_valsA = (uint32_t*)(base + L.sort + 2 * p->total * ts);
+        p->d_valsB = (uint32_t*)(base + L.sort + 2 * p->total * ts + p->total * 4);
+        p->d_spec = (double2*)(base + L.sort);
+    }
+    p->d_hist = (uint32_t*)(base + L.hist);
+    p->d_cbase = (uint32_t*)(base + L.cbase);
+    size_t tw_at = L.tw, cls_at = L.cls, rx_at = L.rx, aux_at = L.aux;
+    size_t twb = 0;
     for (auto& k : p->classes) {
         if (k.bucket) {
             k.d_aux = (uint32_t*)(base + aux_at);
@@ -286,6 +377,7 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         }
         k.d_tw = base + tw_at;
         tw_at += align_up((((size_t)1 << k.log2n) / 2) * 2 * ts, 256);
+        twb += align_up((((size_t)1 << k.log2n) / 2) * 2 * ts, 256);
         k.d_curves = (int*)(base + cls_at);
         cls_at += sizeof(int) * k.h_curves.size();
         const size_t rx = prec == LC_FP32 ? (size_t)k.ncurves * resident_exchange_floats(k.log2n) * 4 : 0;
@@ -297,8 +389,8 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
     p->tw_bytes = twb;
     std::vector<int> tab_all, tab_cls;
     if (p->ntab) {
-        p->d_tab = (double*)(base + o_tab);
-        p->d_tab_curves = (int*)(base + o_tabc);
+        p->d_tab = (double*)(base + L.tab);
+        p->d_tab_curves = (int*)(base + L.tabc);
         for (size_t c = 0; c < njobs; ++c)
             if (p->h_curves[c].kind != LC_ERDF_SHARP) tab_all.push_back((int)c);
         for (auto& k : p->classes) {
@@ -309,14 +401,15 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
         tab_all.insert(tab_all.end(), tab_cls.begin(), tab_cls.end());
     }
 
-    auto fail = [&](const char* what, cudaError_t e) {
-        set_error(std::string(what) + ": " + cudaGetErrorString(e));
-        cudaFree(p->arena);
+    auto fail = [&](const char* what, cudaError_t e2) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e2));
+        if (p->ext) cudaFreeAsync(p->arena, p->stream);
+        else cudaFree(p->arena);
+        cudaStreamSynchronize(p->stream);
+        cudaStreamDestroy(p->stream);
         delete p;
         return LC_ERR_CUDA;
     };
-    cudaError_t e;
-    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail("stream", e);
     cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming);
     cudaEventCreate(&p->t_setup0);
@@ -333,11 +426,15 @@ lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int d
                                         cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
         return fail("upload table curves", e);
     lc_status st = prec == LC_FP32 ? build_tables<float>(*p) : build_tables<double>(*p);
-    if (st != LC_OK) { cudaFree(p->arena); delete p; return st; }
+    if (st != LC_OK) return fail("twiddle tables", cudaGetLastError());
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail("plan sync", e);
-    for (auto& k : p->classes) k.resident = resident_supported(*p, k.log2n);
     *out = p;
     return LC_OK;
+}
+
+lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device, Plan** out)
+{
+    return plan_create_ext(jobs, njobs, prec, device, nullptr, nullptr, out);
 }
 
 // ------------------------------------------------------------ stages
@@ -484,7 +581,12 @@ void plan_free(Plan* p)
         DeviceGuard g(p->device);
         cudaStreamSynchronize(p->stream);
         if (p->iter_graph) cudaGraphExecDestroy(p->iter_graph);
-        cudaFree(p->arena);
+        if (p->ext) {
+            cudaFreeAsync(p->arena, p->stream);
+            cudaStreamSynchronize(p->stream);
+        } else {
+            cudaFree(p->arena);
+        }
         if (p->conv_arena) cudaFree(p->conv_arena);
         if (p->d_tk_stage) cudaFree(p->d_tk_stage);
         cudaEventDestroy(p->ev_in);

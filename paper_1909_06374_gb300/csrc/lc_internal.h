@@ -87,6 +87,8 @@ struct Plan {
     int path_mode = 0;        // 0 auto (measured table), 1 resident where possible, 2 multi-kernel
     int res_max_log2 = -1;    // auto mode: longest length on the fused kernels (-1: the built-in table)
 
+    bool ext = false;            // state / FFT / draw / sort buffers are external planes
+
     // convergence test (Sec. 3.2.2, Eq. 4), off until lc_plan_set_convergence
     bool conv_on = false;
     void* conv_arena = nullptr;  // thresholds, delta record, partial sums
@@ -235,6 +237,30 @@ CurveDev curve_from_job(const lc_job& j);
 
 // plan life cycle shared by the batch ABI and the server
 lc_status plan_create(const lc_job* jobs, size_t njobs, lc_precision prec, int device, Plan** out);
+// Large per-sample buffers owned by someone else (the server): curve c of a
+// plan built on them uses samples [off_c, off_c + N_c) of x, f, s, the key and
+// position planes, and entries [h_c, h_c + N_c/2 + 1) of A and spec, h_c =
+// ext_half_offset(off_c).  off_c must be a multiple of N_c (>= 16), so that
+// the half ranges of curves whose sample ranges are disjoint are disjoint.
+struct ExtPlanes {
+    void* x;
+    void* f;
+    void* A;
+    void* s;
+    void* keysA;
+    void* keysB;
+    uint32_t* valsA;
+    uint32_t* valsB;
+    double2* spec;
+};
+size_t ext_half_offset(uint64_t off);
+// bytes of the external planes per sample of capacity
+size_t ext_plane_bytes_per_sample(lc_precision prec);
+lc_status plan_create_ext(const lc_job* jobs, size_t njobs, lc_precision prec, int device, const ExtPlanes* ext,
+                          const uint64_t* ext_off, Plan** out);
+// device bytes plan_create (ext = false) or plan_create_ext (ext = true)
+// allocates for these jobs; no device call
+lc_status plan_arena_bytes(const lc_job* jobs, size_t njobs, lc_precision prec, bool ext, size_t* bytes);
 lc_status plan_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* launches);
 // n_it more iterations from the current iteration index (each curve stops at
 // its own job count)
