@@ -6,11 +6,13 @@
 // Per curve of N = 2^13 .. 2^17 FP32 samples:
 //   k_bk_sample   1024 values of x_adj at a fixed stride, sorted in shared
 //                 memory; 255 of them become the splitters of 256 buckets
-//                 (bucket b holds spl[b-1] <= x < spl[b]);
-//   k_bk_hist     per 2048-element tile: bucket of every element (binary
-//                 search over the splitters; one byte per element kept for
-//                 the scatter) and the tile's bucket counts; the curve's
-//                 minimum and maximum;
+//                 (bucket b holds spl[b-1] <= x < spl[b]); a 4096-cell grid
+//                 over the sample's range with, per cell, the number of
+//                 splitters in earlier cells;
+//   k_bk_hist     per 2048-element tile: bucket of every element (its cell's
+//                 count, plus the splitters of its own cell that do not
+//                 exceed it; one byte per element kept for the scatter) and
+//                 the tile's bucket counts; the curve's minimum and maximum;
 //   k_bk_scan     tile prefixes and bucket bases of the curve, each bucket's
 //                 bounds, and groups of consecutive buckets of at most kBkCap
 //                 elements, appended to the class's list of work items;
@@ -42,7 +44,7 @@ namespace lc {
 
 constexpr int kBkBuckets = 256;
 constexpr int kBkSample = 1024;
-constexpr int kBkSampleThreads = 512;
+constexpr int kBkSampleThreads = 128;
 constexpr int kBkThreads = 256;                  // finish kernel
 constexpr int kBkPer = kBkCap / kBkThreads;      // elements per finish thread
 constexpr int kBkTileThreads = 256;              // histogram and scatter kernels
@@ -51,7 +53,8 @@ constexpr int kBkTileThreads = 256;              // histogram and scatter kernel
 // number of work items appended this iteration), then per curve: splitters
 // (float bits), the curve's min and max (order keys), bucket bases (257), the
 // group count, per-bucket parameters (lower bound, elements per unit value,
-// base, count: 4 words each); then the work items of the finish kernel, one
+// base, count: 4 words each), the bucket-search grid (lo, cells per unit
+// value) and its table (one byte per cell); then the work items of the finish kernel, one
 // per group (e0, n, first bucket, buckets; curve offset lo, hi, class index
 // of the curve, 0: 8 words each), appended in any order.
 constexpr int kAuxHeader = 64;
@@ -61,7 +64,10 @@ constexpr int kAuxMax = 257;
 constexpr int kAuxBase = 258;
 constexpr int kAuxGcount = kAuxBase + kBkBuckets + 1;   // 515
 constexpr int kAuxPar = 516;                            // 16-byte aligned
-constexpr int kAuxCurveWords = ((kAuxPar + 4 * kBkBuckets) + 63) / 64 * 64;
+constexpr int kBkCells = 4096;                          // lookup cells of the bucket search
+constexpr int kAuxGrid = kAuxPar + 4 * kBkBuckets;      // lo (float bits), cells per unit value (float bits)
+constexpr int kAuxLut = kAuxGrid + 4;                   // kBkCells bytes: splitters in earlier cells
+constexpr int kAuxCurveWords = ((kAuxLut + kBkCells / 4) + 63) / 64 * 64;
 
 int bucket_gmax(uint32_t log2n)
 {
@@ -112,49 +118,109 @@ __device__ __forceinline__ bool bk_active(const BkArgs& a, int c)
     return !a.d_iter || (uint32_t)(*a.d_iter) < a.eff_iters[c];
 }
 
-// Number of splitters <= v: the bucket of v (spl ascending, 255 entries used).
-__device__ __forceinline__ uint32_t bucket_of(const float* spl, float v)
+// Cell of v on the bucket-search grid: monotone in v, in [0, kBkCells).
+__device__ __forceinline__ int grid_cell(float v, float lo, float scale)
 {
-    uint32_t b = 0;
-#pragma unroll
-    for (uint32_t st = 128; st >= 1; st >>= 1)
-        if (v >= spl[b + st - 1]) b += st;
+    return max(0, min(__float2int_rz((v - lo) * scale), kBkCells - 1));  // NaN -> 0
+}
+
+// Number of splitters <= v: the bucket of v (spl ascending, 255 entries
+// used).  lut[c] = splitters in cells below c, a lower bound of the bucket of
+// every value of cell c; the splitters of the value's own cell that do not
+// exceed it are counted on top (any splitter of a later cell exceeds it).
+__device__ __forceinline__ uint32_t bucket_of(const float* spl, const uint8_t* lut, float lo, float scale, float v)
+{
+    uint32_t b = lut[grid_cell(v, lo, scale)];
+    while (b < kBkBuckets - 1 && v >= spl[b]) ++b;
     return b;
 }
 
 // ------------------------------------------------------------------ sample
 __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
 {
+    constexpr int PAIRS = kBkSample / 2 / kBkSampleThreads;  // compare-exchange pairs per thread and stage
     const int ci = blockIdx.x;
     if (ci == 0 && threadIdx.x == 0) *a.nitems = 0;  // before the scan kernel appends
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float sm[kBkSample];
+    __shared__ uint32_t cnt[kBkCells];
     const int tid = threadIdx.x;
     const uint64_t off = a.curves[c].off;
     const uint32_t stride = (1u << a.log2n) / kBkSample;
     for (int i = tid; i < kBkSample; i += kBkSampleThreads) sm[i] = a.xadj[off + (uint64_t)i * stride + stride / 2];
+    for (int i = tid; i < kBkCells; i += kBkSampleThreads) cnt[i] = 0u;
     __syncthreads();
-    // bitonic sort, ascending; thread tid owns pair p = tid of every stage
+    // bitonic sort, ascending; thread tid owns pairs tid + q kBkSampleThreads of every stage
     for (int k = 2; k <= kBkSample; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            const int i = 2 * j * (tid / j) + (tid % j);
-            const int l = i + j;
-            const bool up = (i & k) == 0;
-            const float u = sm[i], v = sm[l];
-            if ((u > v) == up) {
-                sm[i] = v;
-                sm[l] = u;
+#pragma unroll
+            for (int q = 0; q < PAIRS; ++q) {
+                const int t = tid + q * kBkSampleThreads;
+                const int i = 2 * j * (t / j) + (t % j);
+                const int l = i + j;
+                const bool up = (i & k) == 0;
+                const float u = sm[i], v = sm[l];
+                if ((u > v) == up) {
+                    sm[i] = v;
+                    sm[l] = u;
+                }
             }
             __syncthreads();
         }
     }
     uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
-    if (tid < kBkBuckets - 1) A[kAuxSpl + tid] = __float_as_uint(sm[(kBkSample / kBkBuckets) * (tid + 1)]);
-    if (tid == kBkBuckets - 1) A[kAuxSpl + tid] = 0x7f800000u;  // +inf, never compared
+    // splitters; the search grid spans the sample's range
+    const float glo = sm[0], ghi = sm[kBkSample - 1];
+    const float d = ghi - glo;
+    const float gscale = d > 0.0f ? (float)kBkCells / d : 0.0f;
+    for (int i = tid; i < kBkBuckets; i += kBkSampleThreads) {
+        if (i < kBkBuckets - 1) {
+            const float v = sm[(kBkSample / kBkBuckets) * (i + 1)];
+            A[kAuxSpl + i] = __float_as_uint(v);
+            atomicAdd(&cnt[grid_cell(v, glo, gscale)], 1u);
+        } else {
+            A[kAuxSpl + i] = 0x7f800000u;  // +inf, never compared
+        }
+    }
     if (tid == 0) {
         A[kAuxMin] = 0xffffffffu;
         A[kAuxMax] = 0u;
+        A[kAuxGrid] = __float_as_uint(glo);
+        A[kAuxGrid + 1] = __float_as_uint(gscale);
+    }
+    __syncthreads();
+    // lut[c] = splitters in cells below c: exclusive scan of the cell counts
+    // (thread tid owns kBkCells / threads consecutive cells)
+    {
+        constexpr int PER = kBkCells / kBkSampleThreads;  // 32
+        const int c0 = tid * PER;
+        uint32_t run = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) run += cnt[c0 + q];
+        const int lane = tid & 31, warp = tid >> 5;
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __shared__ uint32_t wsum[kBkSampleThreads / 32];
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t acc = incl - run;
+        for (int w = 0; w < warp; ++w) acc += wsum[w];
+        uint32_t* lut = A + kAuxLut;
+#pragma unroll
+        for (int q = 0; q < PER; q += 4) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                word |= min(acc, 255u) << (8 * t);
+                acc += cnt[c0 + q + t];
+            }
+            lut[(c0 + q) / 4] = word;
+        }
     }
 }
 
@@ -172,11 +238,15 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float spl[kBkBuckets];
+    __shared__ uint32_t lutw[kBkCells / 4];
     __shared__ uint32_t h[TPB][kBkBuckets];
     __shared__ uint32_t red[2][W];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
     spl[tid] = __uint_as_float(A[kAuxSpl + tid]);
+    for (int i = tid; i < kBkCells / 4; i += kBkTileThreads) lutw[i] = A[kAuxLut + i];
+    const float glo = __uint_as_float(A[kAuxGrid]), gscale = __uint_as_float(A[kAuxGrid + 1]);
+    const uint8_t* lut = (const uint8_t*)lutw;
 #pragma unroll
     for (int u = 0; u < TPB; ++u) h[u][tid] = 0;
     const uint64_t off = a.curves[c].off;
@@ -197,7 +267,7 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
         uint32_t word = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const uint32_t b = bucket_of(spl, vv[j]);
+            const uint32_t b = bucket_of(spl, lut, glo, gscale, vv[j]);
             atomicAdd(&h[u][b], 1u);
             word |= b << (8 * j);
             const uint32_t k = order_key(vv[j]);
