@@ -491,12 +491,13 @@ __device__ bool bk_block_pass(const uint32_t* __restrict__ ik, const uint32_t* _
     auto digit = [&](uint32_t k, uint32_t v) -> uint32_t {
         return KEYB ? (order_key(__uint_as_float(k)) >> shift) & 255u : ((v & 0xffffffu) >> shift) & 255u;
     };
-    hist[tid] = 0;  // kBkThreads == 256 digits
+    static_assert(kBkThreads >= 256, "one thread per digit");
+    if (tid < 256) hist[tid] = 0;
     __syncthreads();
     for (int i = tid; i < n; i += kBkThreads) atomicAdd(&hist[digit(ik[i], iv[i])], 1u);
     __syncthreads();
-    if (__syncthreads_or(hist[tid] == (uint32_t)n)) return false;
-    uint32_t base = bk_block_scan(hist[tid], wsum);  // digit tid's first output index
+    if (__syncthreads_or(tid < 256 && hist[tid] == (uint32_t)n)) return false;
+    uint32_t base = bk_block_scan(tid < 256 ? hist[tid] : 0u, wsum);  // digit tid's first output index
     const uint32_t lt = (1u << lane) - 1u;
     for (int c0 = 0; c0 < n; c0 += kBkThreads) {
         for (int q = tid; q < W * 256; q += kBkThreads) (&wc[0][0])[q] = 0;
@@ -514,11 +515,13 @@ __device__ bool bk_block_pass(const uint32_t* __restrict__ ik, const uint32_t* _
         if (valid && below == 0) wc[warp][d] = __popc(peers);
         __syncthreads();
         uint32_t tot = 0;
+        if (tid < 256) {
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const uint32_t x = wc[w][tid];
-            wc[w][tid] = base + tot;
-            tot += x;
+            for (int w = 0; w < W; ++w) {
+                const uint32_t x = wc[w][tid];
+                wc[w][tid] = base + tot;
+                tot += x;
+            }
         }
         __syncthreads();
         if (valid) {
@@ -569,7 +572,7 @@ constexpr int kBkSubPer = 2;
 constexpr int kBkNsub = kBkSubPer * kBkCap;
 
 // Shared memory of the finish kernel (u32 words): values and positions |
-// sub-bucket << 17 in sub-bucket order, sub-bucket starts (nsub + 1),
+// sub-bucket << 18 in sub-bucket order, sub-bucket starts (nsub + 1),
 // cursors (then rank -> position), per-bucket parameters, scan partials.
 constexpr int kFinSk = 0;
 constexpr int kFinSi = kBkCap;
@@ -579,13 +582,14 @@ constexpr int kFinPar = kFinEn + kBkNsub;           // float2 lo/scale, uint2 fi
 constexpr int kFinWs = kFinPar + 4 * kBkBuckets;    // 8
 constexpr int kFinWords = kFinWs + 32;
 static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort scratch");
-static_assert(kBkMaxLog2 <= 17 && kBkNsub <= (1 << 15), "position | sub-bucket << 17 in one word");
+static_assert(kBkMaxLog2 <= 18 && kBkNsub <= (1 << 14), "position | sub-bucket << 18 in one word");
 
 // One work item (a group of consecutive buckets of one curve) per block;
 // blocks past the items appended this iteration return at once.
 __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
 {
-    constexpr uint32_t kPosMask = (1u << 17) - 1u;
+    constexpr uint32_t kPosBits = 18;
+    constexpr uint32_t kPosMask = (1u << kPosBits) - 1u;
     const uint32_t item = blockIdx.x;
     if (item >= *a.nitems) return;
     const uint4 d0 = a.items[2 * item];
@@ -690,7 +694,7 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
         if (p < n) {
             const uint32_t q = atomicAdd(&en[sub[j]], 1u);
             sk[q] = key[j];
-            si[q] = pos[j] | (sub[j] << 17);
+            si[q] = pos[j] | (sub[j] << kPosBits);
         }
     }
     __syncthreads();
@@ -702,7 +706,7 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
         const int q = tid + j * kBkThreads;
         if (q < n) {
             const uint32_t w = si[q];
-            const uint32_t u = w >> 17, p = w & kPosMask;
+            const uint32_t u = w >> kPosBits, p = w & kPosMask;
             const uint32_t s0 = st[u], s1 = st[u + 1];
             uint32_t r = (uint32_t)q;
             if (s1 - s0 > 1u) {
