@@ -22,11 +22,13 @@
 //   k_bk_finish   one work item per block, in shared memory: every bucket is
 //                 split into two sub-buckets per element by linear
 //                 interpolation of the value between the bucket's bounds
-//                 (monotone), the group is counting-sorted by sub-bucket, and
-//                 an element that shares its sub-bucket is ranked among its
-//                 members by (value, position) -- the stable argsort order,
-//                 whatever order the scatter left.  rank = group base + rank
-//                 in the group; the block writes x[position] = s[rank].
+//                 (monotone); the elements are counted per sub-bucket and the
+//                 counts scanned; an element alone in its sub-bucket has the
+//                 sub-bucket's start as rank, the members of a shared one are
+//                 placed side by side and ranked among themselves by (value,
+//                 position) -- the stable argsort order, whatever order the
+//                 scatter left.  rank = group base + rank in the group; the
+//                 block writes x[position] = s[rank].
 // A bucket of more than kBkCap elements (a spike of equal or nearly equal
 // values) is one group of its own, sorted by a block-level LSD radix sort on
 // (value, position) through global memory instead.
@@ -571,25 +573,23 @@ __device__ void bk_oversize(const BkArgs& a, uint64_t off, uint32_t e0, int n, u
 constexpr int kBkSubPer = 2;
 constexpr int kBkNsub = kBkSubPer * kBkCap;
 
-// Shared memory of the finish kernel (u32 words): values and positions |
-// sub-bucket << 18 in sub-bucket order, sub-bucket starts (nsub + 1),
-// cursors (then rank -> position), per-bucket parameters, scan partials.
+// Shared memory of the finish kernel (u32 words): values and positions of
+// the elements that share a sub-bucket, at their sub-bucket's start + arrival
+// index; sub-bucket counts, then starts (nsub + 1); per-bucket parameters;
+// scan partials.
 constexpr int kFinSk = 0;
 constexpr int kFinSi = kBkCap;
 constexpr int kFinSt = 2 * kBkCap;                  // kBkNsub + 1 (+3 pad)
-constexpr int kFinEn = kFinSt + kBkNsub + 4;        // cursors, then perm
-constexpr int kFinPar = kFinEn + kBkNsub;           // float2 lo/scale, uint2 first/count: 4 x 256
+constexpr int kFinPar = kFinSt + kBkNsub + 4;       // float2 lo/scale, uint2 first/count: 4 x 256
 constexpr int kFinWs = kFinPar + 4 * kBkBuckets;    // 8
 constexpr int kFinWords = kFinWs + 32;
 static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort scratch");
-static_assert(kBkMaxLog2 <= 18 && kBkNsub <= (1 << 14), "position | sub-bucket << 18 in one word");
 
 // One work item (a group of consecutive buckets of one curve) per block;
 // blocks past the items appended this iteration return at once.
 __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
 {
-    constexpr uint32_t kPosBits = 18;
-    constexpr uint32_t kPosMask = (1u << kPosBits) - 1u;
+    constexpr uint32_t kPosMask = (1u << 24) - 1u;
     const uint32_t item = blockIdx.x;
     if (item >= *a.nitems) return;
     const uint4 d0 = a.items[2 * item];
@@ -608,17 +608,13 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
     float* sk = (float*)(bsm + kFinSk);
     uint32_t* si = bsm + kFinSi;
     uint32_t* st = bsm + kFinSt;
-    uint32_t* en = bsm + kFinEn;
     float2* plo = (float2*)(bsm + kFinPar);                 // (lower bound, sub-buckets per unit)
     uint2* pof = (uint2*)(bsm + kFinPar + 2 * kBkBuckets);  // (first sub-bucket, sub-buckets)
     uint32_t* wsum = bsm + kFinWs;
     const int tid = threadIdx.x;
-    // every global load of the block in flight first: the group's values and
-    // positions, the sorted draws of its ranks, the buckets' parameters
     const uint32_t* __restrict__ kin = a.keys + off + e0;
     const uint32_t* __restrict__ vin = a.vals + off + e0;
-    const float* __restrict__ s = a.s + off + e0;
-    float key[kBkPer], sv[kBkPer];
+    float key[kBkPer];
     uint32_t pos[kBkPer], sub[kBkPer];
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
@@ -626,7 +622,6 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
         if (p < n) {
             key[j] = __uint_as_float(kin[p]);
             pos[j] = vin[p];
-            sv[j] = s[p];
         }
     }
     static_assert(kBkThreads >= kBkBuckets, "one thread per bucket of a group");
@@ -638,8 +633,9 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
     }
     for (int i = tid; i <= ns; i += kBkThreads) st[i] = 0u;
     __syncthreads();
-    // sub-bucket of every element (kBkSubPer per element of its bucket, by
-    // linear interpolation between the bucket's bounds: monotone in the value)
+    // count: the sub-bucket of every element (kBkSubPer per element of its
+    // bucket, by linear interpolation between the bucket's bounds: monotone in
+    // the value) and its arrival index in it
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
         const int p = tid + j * kBkThreads;
@@ -650,16 +646,18 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
             const uint2 of = pof[bl];
             int q = __float2int_rz((key[j] - ls.x) * ls.y);  // NaN -> 0
             q = max(0, min(q, (int)of.y - 1));
-            sub[j] = of.x + (uint32_t)q;
-            atomicAdd(&st[sub[j]], 1u);
+            const uint32_t u = of.x + (uint32_t)q;
+            const uint32_t old = atomicAdd(&st[u], 1u);
+            sub[j] = u | (old << 16);
         }
     }
     __syncthreads();
-    // exclusive scan of the ns sub-bucket counts (thread tid owns the
-    // consecutive ones from kSc tid); cursors = starts
+    // exclusive scan of the ns sub-bucket counts in place (thread tid owns
+    // the consecutive ones from kSc tid); st[ns] = n
     {
         constexpr int kSc = kBkNsub / kBkThreads;  // 16
         static_assert(kSc % 4 == 0, "16-byte loads");
+        static_assert(kBkNsub <= 65536 && kBkCap <= 65536, "sub-bucket and arrival index in 16 bits each");
         uint32_t cn[kSc];
         const int q0 = tid * kSc;
 #pragma unroll
@@ -680,53 +678,49 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
                 o[t] = run;
                 run += q0 + j + t < ns ? cn[j + t] : 0u;
             }
-            if (q0 + j < ns) {
-                *(uint4*)(st + q0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
-                *(uint4*)(en + q0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
-            }
+            if (q0 + j < ns) *(uint4*)(st + q0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
         }
     }
     __syncthreads();
     if (tid == 0) st[ns] = (uint32_t)n;
+    __syncthreads();
+    // an element alone in its sub-bucket has rank = the sub-bucket's start;
+    // the members of a shared sub-bucket go to start + arrival index
+    uint32_t rk[kBkPer];
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
         const int p = tid + j * kBkThreads;
         if (p < n) {
-            const uint32_t q = atomicAdd(&en[sub[j]], 1u);
-            sk[q] = key[j];
-            si[q] = pos[j] | (sub[j] << kPosBits);
-        }
-    }
-    __syncthreads();
-    // rank in sub-bucket order (the placement left each sub-bucket unordered):
-    // r = start + members with a smaller (value, position); neighbouring
-    // lanes hold neighbouring sub-buckets; en becomes rank -> position
-#pragma unroll
-    for (int j = 0; j < kBkPer; ++j) {
-        const int q = tid + j * kBkThreads;
-        if (q < n) {
-            const uint32_t w = si[q];
-            const uint32_t u = w >> kPosBits, p = w & kPosMask;
-            const uint32_t s0 = st[u], s1 = st[u + 1];
-            uint32_t r = (uint32_t)q;
-            if (s1 - s0 > 1u) {
-                const float k = sk[q];
-                r = s0;
-                for (uint32_t m = s0; m < s1; ++m) {
-                    const float km = sk[m];
-                    const uint32_t pm = si[m] & kPosMask;
-                    r += (km < k || (km == k && pm < p)) ? 1u : 0u;
-                }
+            const uint32_t u = sub[j] & 0xffffu;
+            const uint32_t s0 = st[u];
+            rk[j] = s0;
+            if (st[u + 1] - s0 > 1u) {
+                const uint32_t q = s0 + (sub[j] >> 16);
+                sk[q] = key[j];
+                si[q] = pos[j];
+                rk[j] = 0xffffffffu;  // ranked below
             }
-            en[r] = p;
         }
     }
     __syncthreads();
+    const float* __restrict__ s = a.s + off + e0;
     float* __restrict__ x = a.x_out + off;
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
-        const int r = tid + j * kBkThreads;
-        if (r < n) x[en[r]] = sv[j];
+        const int p = tid + j * kBkThreads;
+        if (p < n) {
+            uint32_t r = rk[j];
+            if (r == 0xffffffffu) {  // rank among the members by (value, position)
+                const uint32_t u = sub[j] & 0xffffu;
+                const uint32_t s0 = st[u], s1 = st[u + 1];
+                r = s0;
+                for (uint32_t m = s0; m < s1; ++m) {
+                    const float km = sk[m];
+                    r += (km < key[j] || (km == key[j] && si[m] < pos[j])) ? 1u : 0u;
+                }
+            }
+            x[pos[j]] = s[r];
+        }
     }
 }
 
