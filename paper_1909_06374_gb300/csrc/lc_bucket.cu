@@ -570,7 +570,7 @@ __device__ void bk_oversize(const BkArgs& a, uint64_t off, uint32_t e0, int n, u
 // Sub-buckets per element of a bucket (linear interpolation of the value
 // between the bucket's bounds): fewer elements share one, so fewer need the
 // comparison step.
-constexpr int kBkSubPer = 2;
+constexpr int kBkSubPer = 1;
 constexpr int kBkNsub = kBkSubPer * kBkCap;
 
 // Shared memory of the finish kernel (u32 words): values and positions of
