@@ -587,7 +587,7 @@ static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort sc
 
 // One work item (a group of consecutive buckets of one curve) per block;
 // blocks past the items appended this iteration return at once.
-__global__ void __launch_bounds__(kBkThreads, 5) k_bk_finish(const BkArgs a)
+__global__ void __launch_bounds__(kBkThreads, 6) k_bk_finish(const BkArgs a)
 {
     constexpr uint32_t kPosMask = (1u << 24) - 1u;
     const uint32_t item = blockIdx.x;
