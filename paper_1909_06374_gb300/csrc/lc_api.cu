@@ -493,11 +493,12 @@ static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches, Kern
         }
         if (kt) kt->end(st);
         if (!p.conv_on) {
-            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, nullptr, kt);
+            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, nullptr, kt, k.log2n - 1 >= 12);
         } else {
             // the last sort pass reads keys A, so x_i can go to keys B; Eq. 4
             // then compares it with x_{i-1} in one coalesced pass
-            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, p.d_keysB, kt);
+            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, p.d_keysB, kt,
+                           k.log2n - 1 >= 12);
             if (kt) kt->begin(kGroupOther, st);
             launch_conv_delta<T>(p, k, p.d_keysB, st);
             launch_conv_finalize(p, k, st);

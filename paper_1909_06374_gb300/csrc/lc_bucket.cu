@@ -51,14 +51,15 @@ constexpr int kBkThreads = 256;                  // finish kernel
 constexpr int kBkPer = kBkCap / kBkThreads;      // elements per finish thread
 constexpr int kBkTileThreads = 256;              // histogram and scatter kernels
 
-// Auxiliary area of a class (u32 words): a 64-word header (word 0: the
-// number of work items appended this iteration), then per curve: splitters
-// (float bits), the curve's min and max (order keys), bucket bases (257), the
-// group count, per-bucket parameters (lower bound, elements per unit value,
-// base, count: 4 words each), the bucket-search grid (lo, cells per unit
-// value) and its table (one byte per cell); then the work items of the finish kernel, one
-// per group (e0, n, first bucket, buckets; curve offset lo, hi, class index
-// of the curve, 0: 8 words each), appended in any order.
+// Auxiliary area of a class (u32 words): a 64-word header (unused), then per
+// curve: splitters (float bits), the curve's min and max (order keys), bucket
+// bases (257), the group count, per-bucket parameters (lower bound, elements
+// per unit value, base, count: 4 words each), the bucket-search grid (lo,
+// cells per unit value) and its table (one byte per cell), the sample of
+// x_adj (kBkSample floats, written by the inverse transform's last pass);
+// then the work items of the finish kernel, gmax slots per curve (e0, n,
+// first bucket, buckets; curve offset lo, hi, class index of the curve, 0: 8
+// words each; n = 0 in the slots after the curve's groups).
 constexpr int kAuxHeader = 64;
 constexpr int kAuxSpl = 0;
 constexpr int kAuxMin = 256;
@@ -69,7 +70,27 @@ constexpr int kAuxPar = 516;                            // 16-byte aligned
 constexpr int kBkCells = 4096;                          // lookup cells of the bucket search
 constexpr int kAuxGrid = kAuxPar + 4 * kBkBuckets;      // lo (float bits), cells per unit value (float bits)
 constexpr int kAuxLut = kAuxGrid + 4;                   // kBkCells bytes: splitters in earlier cells
-constexpr int kAuxCurveWords = ((kAuxLut + kBkCells / 4) + 63) / 64 * 64;
+constexpr int kAuxSmp = (kAuxLut + kBkCells / 4 + 3) / 4 * 4;  // kBkSample floats
+constexpr int kAuxCurveWords = ((kAuxSmp + kBkSample) + 63) / 64 * 64;
+
+float* bucket_sample_area(const ClassInfo& k)
+{
+    return (float*)(k.d_aux + kAuxHeader + kAuxSmp);
+}
+
+int bucket_curve_words()
+{
+    return kAuxCurveWords;
+}
+
+// Sample i of a curve of N = 2^log2n samples is x_adj[i N/kBkSample +
+// N/(2 kBkSample)], the real part of complex element d = i 2^shift +
+// 2^(shift-1) with 2^shift = N / (2 kBkSample).
+uint32_t bucket_sample_shift(uint32_t log2n)
+{
+    return log2n - 11;
+}
+static_assert(kBkSample == 1024, "sample shift");
 
 int bucket_gmax(uint32_t log2n)
 {
@@ -99,9 +120,9 @@ struct BkArgs {
     const uint32_t* eff_iters;
     const int* d_iter;       // null: every curve active
     const float* xadj;       // values to rank (the inverse transform's output)
+    int presampled;          // the sample is in the aux area already
     uint32_t* aux;           // [ci][kAuxCurveWords]
-    uint32_t* nitems;        // work items appended this iteration
-    uint4* items;            // [2 * item]: e0, n, first bucket, buckets; off lo, hi, ci, 0
+    uint4* items;            // [2 * (ci gmax + g)]: e0, n, first bucket, buckets; off lo, hi, ci, 0
     uint32_t* hist;          // [ci][tpc][256]
     uint32_t* bid;           // bucket of every element, one byte each (four per word)
     uint32_t* keys;          // bucket order: value bits
@@ -142,24 +163,29 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
 {
     constexpr int PAIRS = kBkSample / 2 / kBkSampleThreads;  // compare-exchange pairs per thread and stage
     const int ci = blockIdx.x;
-    if (ci == 0 && threadIdx.x == 0) *a.nitems = 0;  // before the scan kernel appends
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float sm[kBkSample];
     __shared__ uint32_t cnt[kBkCells];
     const int tid = threadIdx.x;
-    const uint64_t off = a.curves[c].off;
-    const uint32_t stride = (1u << a.log2n) / kBkSample;
-    for (int i = tid; i < kBkSample; i += kBkSampleThreads) sm[i] = a.xadj[off + (uint64_t)i * stride + stride / 2];
+    const uint32_t* A0 = a.aux + (size_t)ci * kAuxCurveWords;
+    if (a.presampled) {
+        for (int i = tid; i < kBkSample; i += kBkSampleThreads) sm[i] = __uint_as_float(A0[kAuxSmp + i]);
+    } else {
+        const uint64_t off = a.curves[c].off;
+        const uint32_t stride = (1u << a.log2n) / kBkSample;
+        for (int i = tid; i < kBkSample; i += kBkSampleThreads) sm[i] = a.xadj[off + (uint64_t)i * stride + stride / 2];
+    }
     for (int i = tid; i < kBkCells; i += kBkSampleThreads) cnt[i] = 0u;
     __syncthreads();
-    // bitonic sort, ascending; thread tid owns pairs tid + q kBkSampleThreads of every stage
+    // bitonic sort, ascending; thread tid owns pairs tid + q kBkSampleThreads of
+    // every stage (j = 2^lj: pair t compares i = 2j (t / j) + t % j with i + j)
     for (int k = 2; k <= kBkSample; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int j = k >> 1, lj = __ffs(k) - 2; j > 0; j >>= 1, --lj) {
 #pragma unroll
             for (int q = 0; q < PAIRS; ++q) {
                 const int t = tid + q * kBkSampleThreads;
-                const int i = 2 * j * (t / j) + (t % j);
+                const int i = ((t >> lj) << (lj + 1)) | (t & (j - 1));
                 const int l = i + j;
                 const bool up = (i & k) == 0;
                 const float u = sm[i], v = sm[l];
@@ -303,17 +329,23 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
 }
 
 // ------------------------------------------------------------------ scan
-// One block (256 threads, thread b = bucket b) per curve.
+// One block (256 threads, thread b = bucket b) per curve.  The curve's groups
+// take its gmax work-item slots in order; the slots after them are marked
+// empty (n = 0), and so are all of them for a curve that has stopped.
 __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
 {
     const int ci = blockIdx.x;
     const int c = a.cls_curves[ci];
-    if (!bk_active(a, c)) return;
+    uint4* items = a.items + 2 * (size_t)ci * a.gmax;
+    if (!bk_active(a, c)) {
+        for (int g = threadIdx.x; g < a.gmax; g += kBkBuckets) items[2 * g] = make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
     __shared__ uint32_t wsum[kBkBuckets / 32];
     __shared__ uint32_t cnt[kBkBuckets];
     __shared__ uint32_t bs[kBkBuckets + 1];
     __shared__ uint32_t gs[kBkBuckets + 1];
-    __shared__ uint32_t ng, first;
+    __shared__ uint32_t ng;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* h = a.hist + (size_t)ci * a.tpc * kBkBuckets + tid;
     uint32_t run = 0;
@@ -372,14 +404,17 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
         gs[g + 1] = kBkBuckets;
         ng = g + 1;
         A[kAuxGcount] = g + 1;
-        first = atomicAdd(a.nitems, g + 1);
     }
     __syncthreads();
     const uint64_t off = a.curves[c].off;
-    for (int g = tid; g < (int)ng; g += kBkBuckets) {
-        const uint32_t b0 = gs[g], b1 = gs[g + 1];
-        a.items[2 * (first + g)] = make_uint4(bs[b0], bs[b1] - bs[b0], b0, b1 - b0);
-        a.items[2 * (first + g) + 1] = make_uint4((uint32_t)off, (uint32_t)(off >> 32), (uint32_t)ci, 0u);
+    for (int g = tid; g < a.gmax; g += kBkBuckets) {
+        if (g < (int)ng) {
+            const uint32_t b0 = gs[g], b1 = gs[g + 1];
+            items[2 * g] = make_uint4(bs[b0], bs[b1] - bs[b0], b0, b1 - b0);
+            items[2 * g + 1] = make_uint4((uint32_t)off, (uint32_t)(off >> 32), (uint32_t)ci, 0u);
+        } else {
+            items[2 * g] = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
 }
 
@@ -585,13 +620,12 @@ constexpr int kFinWs = kFinPar + 4 * kBkBuckets;    // 8
 constexpr int kFinWords = kFinWs + 32;
 static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort scratch");
 
-// One work item (a group of consecutive buckets of one curve) per block;
-// blocks past the items appended this iteration return at once.
+// One work-item slot per block (gmax slots per curve); a block whose slot is
+// empty returns at once.
 __global__ void __launch_bounds__(kBkThreads, 6) k_bk_finish(const BkArgs a)
 {
     constexpr uint32_t kPosMask = (1u << 24) - 1u;
     const uint32_t item = blockIdx.x;
-    if (item >= *a.nitems) return;
     const uint4 d0 = a.items[2 * item];
     const uint4 d1 = a.items[2 * item + 1];
     const uint32_t e0 = d0.x, b0 = d0.z;
@@ -732,15 +766,15 @@ cudaError_t bucket_kernel_attributes()
 }
 
 void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, void* x_out, bool gated,
-                           cudaStream_t st, uint64_t* launches, KernelTimes* kt)
+                           bool presampled, cudaStream_t st, uint64_t* launches, KernelTimes* kt)
 {
     BkArgs a{};
+    a.presampled = presampled ? 1 : 0;
     a.cls_curves = k.d_curves;
     a.curves = p.d_curves;
     a.eff_iters = p.d_eff_iters;
     a.d_iter = gated ? p.d_iter : nullptr;
     a.xadj = (const float*)src;
-    a.nitems = k.d_aux;
     a.aux = k.d_aux + kAuxHeader;
     a.items = (uint4*)(k.d_aux + kAuxHeader + (size_t)k.ncurves * kAuxCurveWords);
     a.hist = p.d_hist + k.hist_off;

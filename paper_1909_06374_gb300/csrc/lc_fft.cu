@@ -104,6 +104,13 @@ struct PassArgs {
     int ncurves;
     uint32_t log2M;
     uint32_t log2p;
+    // inverse last pass of a sample-sorted class: every (M/2^(smp_shift))-th
+    // output's real part, at complex index d with d mod 2^smp_shift =
+    // 2^(smp_shift-1), also goes to smp[ci smp_words + d >> smp_shift] (null:
+    // no sample)
+    float* smp;
+    uint32_t smp_words;
+    uint32_t smp_shift;
 };
 
 // One radix-R Stockham pass (decimation in time, natural-order output) over
@@ -281,16 +288,24 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     __syncthreads();
     tile_dft<T, INV, LR, C>(b0, tw, (int)a.log2M);
     const V* in = b0;
+    const uint32_t smask = (1u << a.smp_shift) - 1u, shalf = (smask + 1u) >> 1;
+    float* const smp = INV && a.smp ? a.smp + (size_t)ci * a.smp_words : nullptr;
     if (p >= (uint32_t)C) {
         for (int idx = threadIdx.x; idx < R * C; idx += 256) {
             const int q = idx >> LC, j = idx & (C - 1);
             const uint32_t i = i0 + (uint32_t)j, k = i & (p - 1);
-            dst[((i - k) << LR) + k + (uint32_t)q * p] = in[q * S + j];
+            const uint32_t d = ((i - k) << LR) + k + (uint32_t)q * p;
+            const V y = in[q * S + j];
+            dst[d] = y;
+            if (smp && (d & smask) == shalf) smp[d >> a.smp_shift] = (float)y.x;
         }
     } else {  // p == 1 (the host guarantees p == 1 or p >= C): column i owns y[i R .. i R + R)
         for (int idx = threadIdx.x; idx < R * C; idx += 256) {
             const int j = idx >> LR, q = idx & (R - 1);
-            dst[((i0 + (uint32_t)j) << LR) + (uint32_t)q] = in[q * S + j];
+            const uint32_t d = ((i0 + (uint32_t)j) << LR) + (uint32_t)q;
+            const V y = in[q * S + j];
+            dst[d] = y;
+            if (smp && (d & smask) == shalf) smp[d >> a.smp_shift] = (float)y.x;
         }
     }
 }
@@ -700,7 +715,7 @@ void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void
                  bool gated, cudaStream_t st, uint64_t* launches, void* scratch)
 {
     if (k.log2n - 1 >= 12) {
-        PassArgs a;
+        PassArgs a{};
         a.cls_curves = k.d_curves;
         a.curves = p.d_curves;
         a.eff_iters = p.d_eff_iters;
@@ -727,7 +742,7 @@ void* launch_fft(const Plan& p, const ClassInfo& k, bool inverse, void* in, void
         }
         return cur;
     }
-    PassArgs a;
+    PassArgs a{};
     a.cls_curves = k.d_curves;
     a.curves = p.d_curves;
     a.eff_iters = p.d_eff_iters;
@@ -785,7 +800,7 @@ template <typename T>
 void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b, void* c, cudaStream_t st,
                            uint64_t* launches)
 {
-    PassArgs a;
+    PassArgs a{};
     a.cls_curves = k.d_curves;
     a.curves = p.d_curves;
     a.eff_iters = p.d_eff_iters;
@@ -835,6 +850,11 @@ void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b,
     log2p = (uint32_t)LR;
     for (int q = P - 2; q >= 0; --q) {
         a.in = cur; a.out = nxt; a.log2p = log2p;
+        if (q == 0 && k.bucket && sizeof(T) == 4) {  // the sample sort's sample of x_adj
+            a.smp = bucket_sample_area(k);
+            a.smp_words = (uint32_t)bucket_curve_words();
+            a.smp_shift = bucket_sample_shift(k.log2n);
+        }
         launch_tile<T, true>(lr[q], a, tile_blocks<T>(k.ncurves, a.log2M, lr[q]), st);
         if (launches) ++*launches;
         log2p += (uint32_t)lr[q];

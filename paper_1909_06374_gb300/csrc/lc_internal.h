@@ -175,10 +175,12 @@ constexpr int kScanChunk = 32;
 enum SortMode { kSortArgsortScatter = 1, kSortKeysToValues = 2 };
 // Stable LSD radix sort of each curve's values `src` (order keys of T):
 // kSortArgsortScatter writes x[perm[r]] = s[r] (x = x_out, default the
-// state); kSortKeysToValues writes the sorted values to s.
+// state); kSortKeysToValues writes the sorted values to s.  presampled: src
+// is the iteration's x_adj, whose sample the inverse transform's last pass
+// has written for the sample-sorted classes.
 template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode,
                                        bool gated, cudaStream_t st, uint64_t* launches, void* x_out = nullptr,
-                                       KernelTimes* kt = nullptr);
+                                       KernelTimes* kt = nullptr, bool presampled = false);
 // sample-sort argsort of the iteration (lc_bucket.cu): FP32 curves of
 // 2^kBkMinLog2 .. 2^kBkMaxLog2 samples (256 buckets of N/256 elements on
 // average); groups of at most kBkCap elements are ranked in shared memory
@@ -193,7 +195,13 @@ size_t bucket_aux_words(uint32_t log2n, int ncurves);  // u32 words of a class
 cudaError_t bucket_kernel_attributes();
 // x_out[perm[r]] = s[r] with perm the stable argsort of `src` (gated).
 void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, void* x_out, bool gated,
-                           cudaStream_t st, uint64_t* launches, KernelTimes* kt);
+                           bool presampled, cudaStream_t st, uint64_t* launches, KernelTimes* kt);
+// where the inverse transform's last pass writes the class's samples of
+// x_adj (curve ci at + ci bucket_curve_words() floats), and the shift of
+// their complex index (PassArgs::smp_shift)
+float* bucket_sample_area(const ClassInfo& k);
+int bucket_curve_words();
+uint32_t bucket_sample_shift(uint32_t log2n);
 // Eq. 4 partial sums of a multi-kernel class between the state x_{i-1} and
 // the new iterate x_i in `xnew` (one double per sort tile, curve-major, in
 // conv.part), moving x_i into the state; for launch_conv_finalize.

@@ -163,7 +163,8 @@ extern "C" lc_status lc_generate_noalloc(const lc_job* job, void* out_x, void* s
                     launch_spectral_iter<float>(p, k, R1, Zp, s);
                     R3 = launch_fft<float>(p, k, true, Zp, R1, nullptr, true, s, nullptr);
                 }
-                launch_sort<float>(p, k, R3, kSortArgsortScatter, true, s, nullptr);
+                launch_sort<float>(p, k, R3, kSortArgsortScatter, true, s, nullptr, nullptr, nullptr,
+                                   k.log2n - 1 >= 12);
                 launch_iter_increment(p, s);
             }
         }

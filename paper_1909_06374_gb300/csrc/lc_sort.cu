@@ -532,10 +532,10 @@ static void launch_hist(bool first, const SortArgs& a, int ncurves, cudaStream_t
 
 template <typename T>
 void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode, bool gated,
-                 cudaStream_t st, uint64_t* launches, void* x_out, KernelTimes* kt)
+                 cudaStream_t st, uint64_t* launches, void* x_out, KernelTimes* kt, bool presampled)
 {
     if (mode == kSortArgsortScatter && k.bucket) {
-        launch_bucket_argsort(p, k, src, x_out, gated, st, launches, kt);
+        launch_bucket_argsort(p, k, src, x_out, gated, presampled, st, launches, kt);
         return;
     }
     using K = typename key_of<T>::type;
@@ -583,8 +583,8 @@ void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mo
 }
 
 template void launch_sort<float>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t, uint64_t*,
-                                void*, KernelTimes*);
+                                void*, KernelTimes*, bool);
 template void launch_sort<double>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t,
-                                 uint64_t*, void*, KernelTimes*);
+                                 uint64_t*, void*, KernelTimes*, bool);
 
 }  // namespace lc
