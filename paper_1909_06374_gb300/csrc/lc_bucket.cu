@@ -4,31 +4,33 @@
 // that ranks every element exactly.
 //
 // Per curve of N = 2^13 .. 2^17 FP32 samples:
-//   k_bk_sample   1024 values of x_adj at a fixed stride, sorted in shared
-//                 memory; 255 of them become the splitters of 256 buckets
-//                 (bucket b holds spl[b-1] <= x < spl[b]); a 4096-cell grid
-//                 over the sample's range with, per cell, the number of
-//                 splitters in earlier cells;
+//   k_bk_sample   1024 values of x_adj at a fixed stride (stored by the
+//                 inverse transform's last pass, or gathered here), sorted in
+//                 shared memory; 255 of them become the splitters of 256
+//                 buckets (bucket b holds spl[b-1] <= x < spl[b]); a
+//                 4096-cell grid over the sample's range with, per cell, the
+//                 number of splitters in earlier cells;
 //   k_bk_hist     per 2048-element tile: bucket of every element (its cell's
 //                 count, plus the splitters of its own cell that do not
 //                 exceed it; one byte per element kept for the scatter) and
-//                 the tile's bucket counts; the curve's minimum and maximum;
+//                 the tile's bucket counts;
 //   k_bk_scan     tile prefixes and bucket bases of the curve, each bucket's
 //                 bounds, and groups of consecutive buckets of at most kBkCap
-//                 elements, appended to the class's list of work items;
+//                 elements, in the curve's own work-item slots;
 //   k_bk_scatter  per tile: the elements placed in shared memory in bucket
 //                 order (the order inside a bucket is arbitrary), then each
 //                 bucket's run written to the tile's slice of the bucket;
 //   k_bk_finish   one work item per block, in shared memory: every bucket is
 //                 split into two sub-buckets per element by linear
 //                 interpolation of the value between the bucket's bounds
-//                 (monotone); the elements are counted per sub-bucket and the
-//                 counts scanned; an element alone in its sub-bucket has the
-//                 sub-bucket's start as rank, the members of a shared one are
-//                 placed side by side and ranked among themselves by (value,
-//                 position) -- the stable argsort order, whatever order the
-//                 scatter left.  rank = group base + rank in the group; the
-//                 block writes x[position] = s[rank].
+//                 (monotone; values beyond the sample's extremes go to the
+//                 edge sub-buckets); the elements are counted per sub-bucket
+//                 and the counts scanned; an element alone in its sub-bucket
+//                 has the sub-bucket's start as rank, the members of a shared
+//                 one are placed side by side and ranked among themselves by
+//                 (value, position) -- the stable argsort order, whatever
+//                 order the scatter left.  rank = group base + rank in the
+//                 group; the block writes x[position] = s[rank].
 // A bucket of more than kBkCap elements (a spike of equal or nearly equal
 // values) is one group of its own, sorted by a block-level LSD radix sort on
 // (value, position) through global memory instead.
@@ -212,8 +214,10 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
         }
     }
     if (tid == 0) {
-        A[kAuxMin] = 0xffffffffu;
-        A[kAuxMax] = 0u;
+        // the sample's extremes bound the first and the last bucket (values
+        // beyond them go to those buckets' edge sub-buckets)
+        A[kAuxMin] = order_key(glo);
+        A[kAuxMax] = order_key(ghi);
         A[kAuxGrid] = __float_as_uint(glo);
         A[kAuxGrid + 1] = __float_as_uint(gscale);
     }
@@ -253,12 +257,11 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
 }
 
 // ------------------------------------------------------------------ histogram
-// TPB tiles per block: bucket counts per tile, the bucket of every element
-// (one byte, packed four to a word, for the scatter), the tiles' min / max.
+// TPB tiles per block: bucket counts per tile and the bucket of every element
+// (one byte, packed four to a word, for the scatter).
 template <int TPB>
 __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
 {
-    constexpr int W = kBkTileThreads / 32;
     constexpr int V4 = kSortTile / 4 / kBkTileThreads;  // float4 loads per thread and tile
     const int bpc = a.tpc / TPB;
     const int ci = blockIdx.x / bpc;
@@ -268,8 +271,7 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
     __shared__ float spl[kBkBuckets];
     __shared__ uint32_t lutw[kBkCells / 4];
     __shared__ uint32_t h[TPB][kBkBuckets];
-    __shared__ uint32_t red[2][W];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
     spl[tid] = __uint_as_float(A[kAuxSpl + tid]);
     for (int i = tid; i < kBkCells / 4; i += kBkTileThreads) lutw[i] = A[kAuxLut + i];
@@ -287,7 +289,6 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
         q[e] = src[(size_t)u * (kSortTile / 4) + v];
     }
     __syncthreads();
-    uint32_t kmin = 0xffffffffu, kmax = 0u;
 #pragma unroll
     for (int e = 0; e < TPB * V4; ++e) {
         const int u = e / V4, v = tid + (e % V4) * kBkTileThreads;
@@ -298,34 +299,12 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
             const uint32_t b = bucket_of(spl, lut, glo, gscale, vv[j]);
             atomicAdd(&h[u][b], 1u);
             word |= b << (8 * j);
-            const uint32_t k = order_key(vv[j]);
-            kmin = min(kmin, k);
-            kmax = max(kmax, k);
         }
         bid[(size_t)u * (kSortTile / 4) + v] = word;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-    }
-    if (lane == 0) {
-        red[0][warp] = kmin;
-        red[1][warp] = kmax;
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < TPB; ++u) a.hist[((size_t)ci * a.tpc + t0 + u) * kBkBuckets + tid] = h[u][tid];
-    if (tid == 0) {
-        uint32_t m0 = red[0][0], m1 = red[1][0];
-#pragma unroll
-        for (int w = 1; w < W; ++w) {
-            m0 = min(m0, red[0][w]);
-            m1 = max(m1, red[1][w]);
-        }
-        atomicMin(&A[kAuxMin], m0);
-        atomicMax(&A[kAuxMax], m1);
-    }
 }
 
 // ------------------------------------------------------------------ scan
@@ -604,18 +583,20 @@ __device__ void bk_oversize(const BkArgs& a, uint64_t off, uint32_t e0, int n, u
 
 // Sub-buckets per element of a bucket (linear interpolation of the value
 // between the bucket's bounds): fewer elements share one, so fewer need the
-// comparison step.
-constexpr int kBkSubPer = 1;
+// comparison step; their counters are 16 bits wide (two to a word), so two
+// per element cost no more shared memory or scan steps than one 32-bit
+// counter per element.
+constexpr int kBkSubPer = 2;
 constexpr int kBkNsub = kBkSubPer * kBkCap;
 
-// Shared memory of the finish kernel (u32 words): values and positions of
-// the elements that share a sub-bucket, at their sub-bucket's start + arrival
-// index; sub-bucket counts, then starts (nsub + 1); per-bucket parameters;
-// scan partials.
-constexpr int kFinSk = 0;
-constexpr int kFinSi = kBkCap;
-constexpr int kFinSt = 2 * kBkCap;                  // kBkNsub + 1 (+3 pad)
-constexpr int kFinPar = kFinSt + kBkNsub + 4;       // float2 lo/scale, uint2 first/count: 4 x 256
+// Shared memory of the finish kernel (u32 words): the 64-bit keys (order key
+// of the value << 32 | position) of the elements that share a sub-bucket, at
+// their sub-bucket's start + arrival index; sub-bucket counts, then starts
+// (nsub + 1, 16 bits each, two to a word); per-bucket parameters; scan
+// partials.
+constexpr int kFinKk = 0;                           // kBkCap u64
+constexpr int kFinSt = 2 * kBkCap;                  // kBkNsub / 2 + 1 words (+3 pad)
+constexpr int kFinPar = kFinSt + kBkNsub / 2 + 4;   // float2 lo/scale, uint2 first/count: 4 x 256
 constexpr int kFinWs = kFinPar + 4 * kBkBuckets;    // 8
 constexpr int kFinWords = kFinWs + 32;
 static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort scratch");
@@ -639,8 +620,7 @@ __global__ void __launch_bounds__(kBkThreads, 6) k_bk_finish(const BkArgs a)
         return;
     }
     const int ns = kBkSubPer * n;  // sub-buckets of the group
-    float* sk = (float*)(bsm + kFinSk);
-    uint32_t* si = bsm + kFinSi;
+    unsigned long long* kk = (unsigned long long*)(bsm + kFinKk);
     uint32_t* st = bsm + kFinSt;
     float2* plo = (float2*)(bsm + kFinPar);                 // (lower bound, sub-buckets per unit)
     uint2* pof = (uint2*)(bsm + kFinPar + 2 * kBkBuckets);  // (first sub-bucket, sub-buckets)
@@ -665,7 +645,8 @@ __global__ void __launch_bounds__(kBkThreads, 6) k_bk_finish(const BkArgs a)
         plo[tid] = make_float2(__uint_as_float(P.x), (float)kBkSubPer * __uint_as_float(P.y));
         pof[tid] = make_uint2((uint32_t)kBkSubPer * (P.z - e0), (uint32_t)kBkSubPer * P.w);
     }
-    for (int i = tid; i <= ns; i += kBkThreads) st[i] = 0u;
+    const int nw = ns / 2;  // words of the 16-bit counters
+    for (int i = tid; i <= nw; i += kBkThreads) st[i] = 0u;
     __syncthreads();
     // count: the sub-bucket of every element (kBkSubPer per element of its
     // bucket, by linear interpolation between the bucket's bounds: monotone in
@@ -681,59 +662,68 @@ __global__ void __launch_bounds__(kBkThreads, 6) k_bk_finish(const BkArgs a)
             int q = __float2int_rz((key[j] - ls.x) * ls.y);  // NaN -> 0
             q = max(0, min(q, (int)of.y - 1));
             const uint32_t u = of.x + (uint32_t)q;
-            const uint32_t old = atomicAdd(&st[u], 1u);
+            const uint32_t sh = (u & 1u) << 4;  // 16-bit counter u: half u & 1 of word u / 2
+            const uint32_t old = (atomicAdd(&st[u >> 1], 1u << sh) >> sh) & 0xffffu;
             sub[j] = u | (old << 16);
         }
     }
     __syncthreads();
-    // exclusive scan of the ns sub-bucket counts in place (thread tid owns
-    // the consecutive ones from kSc tid); st[ns] = n
+    // exclusive scan of the ns 16-bit sub-bucket counts in place (thread tid
+    // owns the consecutive words from kSc tid); st16[ns] = n
+    uint16_t* st16 = (uint16_t*)st;
     {
-        constexpr int kSc = kBkNsub / kBkThreads;  // 16
+        constexpr int kSc = kBkNsub / 2 / kBkThreads;
         static_assert(kSc % 4 == 0, "16-byte loads");
-        static_assert(kBkNsub <= 65536 && kBkCap <= 65536, "sub-bucket and arrival index in 16 bits each");
-        uint32_t cn[kSc];
+        static_assert(kBkNsub <= 65536 && kBkCap <= 65535, "sub-bucket, arrival index and starts in 16 bits");
         const int q0 = tid * kSc;
-#pragma unroll
-        for (int j = 0; j < kSc; j += 4) {
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (q0 + j < ns) v = *(const uint4*)(st + q0 + j);  // words to ns + 3: zeroed or counted
-            cn[j] = v.x; cn[j + 1] = v.y; cn[j + 2] = v.z; cn[j + 3] = v.w;
-        }
+        // the counts are read twice (sum, then prefixes) to keep them out of
+        // registers while the elements' state is live
         uint32_t sum = 0;
 #pragma unroll
-        for (int j = 0; j < kSc; ++j) sum += q0 + j < ns ? cn[j] : 0u;
+        for (int j = 0; j < kSc; j += 4) {
+            if (q0 + j < nw) {
+                const uint4 v = *(const uint4*)(st + q0 + j);  // words to nw + 3: zeroed or counted
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (q0 + j + t < nw) sum += (w[t] & 0xffffu) + (w[t] >> 16);
+            }
+        }
         uint32_t run = bk_block_scan(sum, wsum);
 #pragma unroll
         for (int j = 0; j < kSc; j += 4) {
-            uint32_t o[4];
+            if (q0 + j < nw) {
+                const uint4 v = *(const uint4*)(st + q0 + j);
+                uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                o[t] = run;
-                run += q0 + j + t < ns ? cn[j + t] : 0u;
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t lo = run;
+                    if (q0 + j + t < nw) run += w[t] & 0xffffu;
+                    const uint32_t hi = run;
+                    if (q0 + j + t < nw) run += w[t] >> 16;
+                    w[t] = lo | (hi << 16);
+                }
+                *(uint4*)(st + q0 + j) = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            if (q0 + j < ns) *(uint4*)(st + q0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
         }
     }
     __syncthreads();
-    if (tid == 0) st[ns] = (uint32_t)n;
+    if (tid == 0) st16[ns] = (uint16_t)n;
     __syncthreads();
     // an element alone in its sub-bucket has rank = the sub-bucket's start;
-    // the members of a shared sub-bucket go to start + arrival index
+    // the members of a shared sub-bucket are placed at start + arrival index
+    // and ranked below.  rk[j] = the start; sub[j] = members | arrival << 16
     uint32_t rk[kBkPer];
 #pragma unroll
     for (int j = 0; j < kBkPer; ++j) {
         const int p = tid + j * kBkThreads;
         if (p < n) {
-            const uint32_t u = sub[j] & 0xffffu;
-            const uint32_t s0 = st[u];
+            const uint32_t u = sub[j] & 0xffffu, old = sub[j] >> 16;
+            const uint32_t s0 = st16[u];
+            const uint32_t c = st16[u + 1] - s0;
             rk[j] = s0;
-            if (st[u + 1] - s0 > 1u) {
-                const uint32_t q = s0 + (sub[j] >> 16);
-                sk[q] = key[j];
-                si[q] = pos[j];
-                rk[j] = 0xffffffffu;  // ranked below
-            }
+            if (c > 1u) kk[s0 + old] = ((unsigned long long)order_key(key[j]) << 32) | pos[j];
+            sub[j] = c | (old << 16);
         }
     }
     __syncthreads();
@@ -744,14 +734,14 @@ __global__ void __launch_bounds__(kBkThreads, 6) k_bk_finish(const BkArgs a)
         const int p = tid + j * kBkThreads;
         if (p < n) {
             uint32_t r = rk[j];
-            if (r == 0xffffffffu) {  // rank among the members by (value, position)
-                const uint32_t u = sub[j] & 0xffffu;
-                const uint32_t s0 = st[u], s1 = st[u + 1];
-                r = s0;
-                for (uint32_t m = s0; m < s1; ++m) {
-                    const float km = sk[m];
-                    r += (km < key[j] || (km == key[j] && si[m] < pos[j])) ? 1u : 0u;
-                }
+            const uint32_t c = sub[j] & 0xffffu;
+            if (c > 1u) {
+                // rank among the members by (value, position): one 64-bit
+                // comparison per member (order keys of equal values are
+                // equal, positions break the tie)
+                const unsigned long long K = ((unsigned long long)order_key(key[j]) << 32) | pos[j];
+                const uint32_t s0 = r;
+                for (uint32_t m = s0; m < s0 + c; ++m) r += kk[m] < K ? 1u : 0u;
             }
             x[pos[j]] = s[r];
         }
