@@ -161,44 +161,98 @@ __device__ __forceinline__ uint32_t bucket_of(const float* spl, const uint8_t* l
 }
 
 // ------------------------------------------------------------------ sample
+// Compare-exchange of a bitonic stage: the element with the lower index of the
+// pair keeps the smaller value in an ascending block (bit k of its index 0).
+__device__ __forceinline__ float bitonic_keep(float mine, float other, bool lower, bool up)
+{
+    const bool keep_min = lower == up;
+    return keep_min ? (other < mine ? other : mine) : (other > mine ? other : mine);
+}
+
+// A bitonic stage whose pairs are elements i and i + M of one thread (element
+// index 32 (8 warp + i) + lane): M is a compile-time constant so that v stays
+// in registers.
+template <int M>
+__device__ __forceinline__ void bitonic_in_thread(float (&v)[8], int warp, int lane, int k)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if ((i & M) == 0) {
+            const int e = 32 * (8 * warp + i) + lane;
+            const float x0 = v[i], x1 = v[i + M];
+            const bool up = (e & k) == 0;
+            v[i] = bitonic_keep(x0, x1, true, up);
+            v[i + M] = bitonic_keep(x1, x0, false, up);
+        }
+    }
+}
+
+// Cell-count index with one pad word per 32 cells, so that a thread reading
+// its own 32 consecutive cells meets no bank conflict with its warp.
+__device__ __forceinline__ int cell_slot(int c)
+{
+    return c + (c >> 5);
+}
+
+// One block of 128 threads per curve.  The 1024 sample values are sorted by a
+// bitonic network held in registers: thread (warp w, lane l) keeps element
+// 32 (8 w + i) + l in v[i], i < 8, so the stages with a partner distance j < 32
+// exchange through warp shuffles, those with j = 32, 64, 128 stay inside the
+// thread, and only j = 256 and 512 go through shared memory.
 __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
 {
-    constexpr int PAIRS = kBkSample / 2 / kBkSampleThreads;  // compare-exchange pairs per thread and stage
+    static_assert(kBkSample == 1024 && kBkSampleThreads == 128, "register layout of the sample sort");
+    constexpr int PER = kBkSample / kBkSampleThreads;  // 8 elements per thread
     const int ci = blockIdx.x;
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float sm[kBkSample];
-    __shared__ uint32_t cnt[kBkCells];
-    const int tid = threadIdx.x;
+    __shared__ uint32_t cnt[kBkCells + kBkCells / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t* A0 = a.aux + (size_t)ci * kAuxCurveWords;
-    if (a.presampled) {
-        for (int i = tid; i < kBkSample; i += kBkSampleThreads) sm[i] = __uint_as_float(A0[kAuxSmp + i]);
-    } else {
-        const uint64_t off = a.curves[c].off;
-        const uint32_t stride = (1u << a.log2n) / kBkSample;
-        for (int i = tid; i < kBkSample; i += kBkSampleThreads) sm[i] = a.xadj[off + (uint64_t)i * stride + stride / 2];
-    }
-    for (int i = tid; i < kBkCells; i += kBkSampleThreads) cnt[i] = 0u;
-    __syncthreads();
-    // bitonic sort, ascending; thread tid owns pairs tid + q kBkSampleThreads of
-    // every stage (j = 2^lj: pair t compares i = 2j (t / j) + t % j with i + j)
-    for (int k = 2; k <= kBkSample; k <<= 1) {
-        for (int j = k >> 1, lj = __ffs(k) - 2; j > 0; j >>= 1, --lj) {
+    float v[PER];
 #pragma unroll
-            for (int q = 0; q < PAIRS; ++q) {
-                const int t = tid + q * kBkSampleThreads;
-                const int i = ((t >> lj) << (lj + 1)) | (t & (j - 1));
-                const int l = i + j;
-                const bool up = (i & k) == 0;
-                const float u = sm[i], v = sm[l];
-                if ((u > v) == up) {
-                    sm[i] = v;
-                    sm[l] = u;
-                }
-            }
-            __syncthreads();
+    for (int i = 0; i < PER; ++i) {
+        const int e = 32 * (8 * warp + i) + lane;
+        if (a.presampled) {
+            v[i] = __uint_as_float(A0[kAuxSmp + e]);
+        } else {
+            const uint32_t stride = (1u << a.log2n) / kBkSample;
+            v[i] = a.xadj[a.curves[c].off + (uint64_t)e * stride + stride / 2];
         }
     }
+    for (int i = tid; i < kBkCells + kBkCells / 32; i += kBkSampleThreads) cnt[i] = 0u;
+    // bitonic sort, ascending
+    for (int k = 2; k <= kBkSample; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < 32) {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const int e = 32 * (8 * warp + i) + lane;
+                    const float o = __shfl_xor_sync(0xffffffffu, v[i], j);
+                    v[i] = bitonic_keep(v[i], o, lower, (e & k) == 0);
+                }
+            } else if (j < 256) {  // partner: element i ^ (j / 32) of the same thread
+                if (j == 32) bitonic_in_thread<1>(v, warp, lane, k);
+                else if (j == 64) bitonic_in_thread<2>(v, warp, lane, k);
+                else bitonic_in_thread<4>(v, warp, lane, k);
+            } else {
+#pragma unroll
+                for (int i = 0; i < PER; ++i) sm[32 * (8 * warp + i) + lane] = v[i];
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const int e = 32 * (8 * warp + i) + lane;
+                    v[i] = bitonic_keep(v[i], sm[e ^ j], (e & j) == 0, (e & k) == 0);
+                }
+                __syncthreads();
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) sm[32 * (8 * warp + i) + lane] = v[i];
+    __syncthreads();
     uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
     // splitters; the search grid spans the sample's range
     const float glo = sm[0], ghi = sm[kBkSample - 1];
@@ -206,9 +260,9 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
     const float gscale = d > 0.0f ? (float)kBkCells / d : 0.0f;
     for (int i = tid; i < kBkBuckets; i += kBkSampleThreads) {
         if (i < kBkBuckets - 1) {
-            const float v = sm[(kBkSample / kBkBuckets) * (i + 1)];
-            A[kAuxSpl + i] = __float_as_uint(v);
-            atomicAdd(&cnt[grid_cell(v, glo, gscale)], 1u);
+            const float sv = sm[(kBkSample / kBkBuckets) * (i + 1)];
+            A[kAuxSpl + i] = __float_as_uint(sv);
+            atomicAdd(&cnt[cell_slot(grid_cell(sv, glo, gscale))], 1u);
         } else {
             A[kAuxSpl + i] = 0x7f800000u;  // +inf, never compared
         }
@@ -225,12 +279,12 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
     // lut[c] = splitters in cells below c: exclusive scan of the cell counts
     // (thread tid owns kBkCells / threads consecutive cells)
     {
-        constexpr int PER = kBkCells / kBkSampleThreads;  // 32
-        const int c0 = tid * PER;
+        constexpr int CPT = kBkCells / kBkSampleThreads;  // 32
+        static_assert(CPT == 32, "one padded row of cells per thread");
+        const int c0 = tid * CPT;
         uint32_t run = 0;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) run += cnt[c0 + q];
-        const int lane = tid & 31, warp = tid >> 5;
+        for (int q = 0; q < CPT; ++q) run += cnt[cell_slot(c0 + q)];
         uint32_t incl = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -244,12 +298,12 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
         for (int w = 0; w < warp; ++w) acc += wsum[w];
         uint32_t* lut = A + kAuxLut;
 #pragma unroll
-        for (int q = 0; q < PER; q += 4) {
+        for (int q = 0; q < CPT; q += 4) {
             uint32_t word = 0;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 word |= min(acc, 255u) << (8 * t);
-                acc += cnt[c0 + q + t];
+                acc += cnt[cell_slot(c0 + q + t)];
             }
             lut[(c0 + q) / 4] = word;
         }
@@ -311,8 +365,14 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
 // One block (256 threads, thread b = bucket b) per curve.  The curve's groups
 // take its gmax work-item slots in order; the slots after them are marked
 // empty (n = 0), and so are all of them for a curve that has stopped.
+// Groups: the group that starts at bucket s ends before bucket e = the last
+// index with base[e] - base[s] <= kBkCap (at least s + 1: a larger bucket is a
+// group of its own), found for every s at once by binary search; thread 0
+// then follows these links from bucket 0.  Any two consecutive groups hold
+// more than kBkCap elements, so a curve has at most gmax = 2 N / kBkCap + 1.
 __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
 {
+    constexpr int kChunk = 32;  // tile counts loaded together
     const int ci = blockIdx.x;
     const int c = a.cls_curves[ci];
     uint4* items = a.items + 2 * (size_t)ci * a.gmax;
@@ -321,19 +381,30 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
         return;
     }
     __shared__ uint32_t wsum[kBkBuckets / 32];
-    __shared__ uint32_t cnt[kBkBuckets];
     __shared__ uint32_t bs[kBkBuckets + 1];
+    __shared__ uint32_t nx[kBkBuckets];
     __shared__ uint32_t gs[kBkBuckets + 1];
     __shared__ uint32_t ng;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
+    // the bucket's bounds (read before the counts, so both loads overlap)
+    const float lo = tid == 0 ? key_value(A[kAuxMin]) : __uint_as_float(A[kAuxSpl + tid - 1]);
+    const float hi = tid == kBkBuckets - 1 ? key_value(A[kAuxMax]) : __uint_as_float(A[kAuxSpl + tid]);
+    // bucket tid's count in every tile, replaced by the tile's prefix
     uint32_t* h = a.hist + (size_t)ci * a.tpc * kBkBuckets + tid;
     uint32_t run = 0;
-    for (int t0 = 0; t0 < a.tpc; t0 += 16) {
-        uint32_t v[16];
+    for (int t0 = 0; t0 < a.tpc; t0 += kChunk) {
+        uint32_t v[kChunk];
+        // all of the chunk's loads are issued before any store (the stores
+        // overwrite the same words, so the compiler would otherwise pair them)
 #pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = t0 + u < a.tpc ? h[(size_t)(t0 + u) * kBkBuckets] : 0u;
+        for (int u = 0; u < kChunk; ++u) {
+            v[u] = 0u;
+            if (t0 + u < a.tpc)
+                asm volatile("ld.global.u32 %0, [%1];" : "=r"(v[u]) : "l"(h + (size_t)(t0 + u) * kBkBuckets) : "memory");
+        }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int u = 0; u < kChunk; ++u) {
             if (t0 + u < a.tpc) h[(size_t)(t0 + u) * kBkBuckets] = run;
             run += v[u];
         }
@@ -346,11 +417,9 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
         if (lane >= o) incl += y;
     }
     if (lane == 31) wsum[warp] = incl;
-    cnt[tid] = run;
     __syncthreads();
     uint32_t woff = 0;
     for (int w = 0; w < warp; ++w) woff += wsum[w];
-    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
     const uint32_t base = woff + incl - run;
     A[kAuxBase + tid] = base;
     bs[tid] = base;
@@ -359,30 +428,32 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
         bs[kBkBuckets] = base + run;
     }
     {
-        // the bucket's bounds and its sub-buckets per unit value (one
-        // sub-bucket per element, spread linearly over [lo, hi])
-        const float lo = tid == 0 ? key_value(A[kAuxMin]) : __uint_as_float(A[kAuxSpl + tid - 1]);
-        const float hi = tid == kBkBuckets - 1 ? key_value(A[kAuxMax]) : __uint_as_float(A[kAuxSpl + tid]);
+        // sub-buckets per unit value (spread linearly over [lo, hi])
         const float d = hi - lo;
         const float sc = (d > 0.0f && run > 0u) ? (float)run / d : 0.0f;
         ((uint4*)(A + kAuxPar))[tid] = make_uint4(__float_as_uint(lo), __float_as_uint(sc), base, run);
     }
-    if (tid == 0) {
-        // greedy groups of consecutive buckets holding at most kBkCap
-        // elements; a larger bucket forms a group of its own
-        uint32_t g = 0, acc = 0;
-        gs[0] = 0;
-        for (int b = 0; b < kBkBuckets; ++b) {
-            const uint32_t n = cnt[b];
-            if (acc > 0 && acc + n > (uint32_t)kBkCap) {
-                gs[++g] = (uint32_t)b;
-                acc = 0;
-            }
-            acc += n;
+    __syncthreads();
+    {
+        const uint32_t target = base + (uint32_t)kBkCap;
+        int l = tid + 1, r = kBkBuckets;  // last e in [tid + 1, 256] with bs[e] <= target, else tid + 1
+        while (l < r) {
+            const int mid = (l + r + 1) >> 1;
+            if (bs[mid] <= target) l = mid;
+            else r = mid - 1;
         }
-        gs[g + 1] = kBkBuckets;
-        ng = g + 1;
-        A[kAuxGcount] = g + 1;
+        nx[tid] = (uint32_t)l;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t g = 0, b = 0;
+        while (b < (uint32_t)kBkBuckets) {
+            gs[g++] = b;
+            b = nx[b];
+        }
+        gs[g] = kBkBuckets;
+        ng = g;
+        A[kAuxGcount] = g;
     }
     __syncthreads();
     const uint64_t off = a.curves[c].off;
