@@ -446,24 +446,32 @@ __global__ void __launch_bounds__(256) k_spectral_tk(const SpecArgs a)
 // One conjugate pair (t, M - t) of the spectral step on values held by the
 // caller: za = Z_t, zb = Z_{M-t} in, Z'_t, Z'_{M-t} out.  The arithmetic runs
 // on the representative k = min(t, M - t), as in k_spectral_iter.
+// W = e^{-2 pi i k/N} (rt[k]), Ak = A[k], Am = A[M - k] for k = min(t, M - t),
+// loaded by the caller.
 template <typename T>
-__device__ __forceinline__ void spectral_pair_tk(cplx<T>& za, cplx<T>& zb, uint32_t t, uint32_t M,
-                                                 const cplx<T>* __restrict__ rt, const T* __restrict__ A)
+__device__ __forceinline__ void spectral_pair_vals(cplx<T>& za, cplx<T>& zb, uint32_t t, uint32_t M,
+                                                   const cplx<T> W, const T Ak, const T Am)
 {
     using V = cplx<T>;
     const bool low = 2 * t < M;
-    const uint32_t k = low ? t : M - t;
     const V zk = low ? za : zb, zm = low ? zb : za;
-    const V W = rt[k];
     V E; E.x = (T)0.5 * (zk.x + zm.x); E.y = (T)0.5 * (zk.y - zm.y);
     V O; O.x = (T)0.5 * (zk.y + zm.y); O.y = (T)-0.5 * (zk.x - zm.x);
     const V WO = cmul(W, O);
-    const V Yk = keep_phase(cadd(E, WO), A[k]);
-    const V Ym = keep_phase(cconj(csub(E, WO)), A[M - k]);
+    const V Yk = keep_phase(cadd(E, WO), Ak);
+    const V Ym = keep_phase(cconj(csub(E, WO)), Am);
     V Zk, Zm;
     pack_pair(Yk, Ym, W, Zk, Zm);
     za = low ? Zk : Zm;
     zb = low ? Zm : Zk;
+}
+
+template <typename T>
+__device__ __forceinline__ void spectral_pair_tk(cplx<T>& za, cplx<T>& zb, uint32_t t, uint32_t M,
+                                                 const cplx<T>* __restrict__ rt, const T* __restrict__ A)
+{
+    const uint32_t k = 2 * t < M ? t : M - t;
+    spectral_pair_vals<T>(za, zb, t, M, rt[k], A[k], A[M - k]);
 }
 
 // The middle of one iteration on the tile path, in one kernel: the forward
@@ -527,8 +535,29 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     __syncthreads();
     tile_dft<T, false, LR, C>(b0, tw, (int)a.log2M);
     V* in = b0;
-    // spectral step on the conjugate pairs, in place: in[q][j] = Z_{column(j) + q p}
-    for (int idx = threadIdx.x; idx < R * H; idx += 256) {
+    // spectral step on the conjugate pairs, in place: in[q][j] = Z_{column(j) + q p}.
+    // FP32: the twiddles and amplitudes of all of the thread's pairs are loaded
+    // first, so that their latencies overlap (one wait instead of one per pair).
+    constexpr bool kPre = sizeof(T) == 4;
+    constexpr int NP = kPre ? (R * H + 255) / 256 : 1;
+    V Wp[NP];
+    T Akp[NP], Amp[NP];
+    if (kPre) {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const int idx = threadIdx.x + m * 256;
+            if ((R * H) % 256 == 0 || idx < R * H) {
+                const uint32_t t = column(idx & (H - 1)) + (uint32_t)(idx >> LH) * p;
+                const uint32_t k = 2 * t < M ? t : M - t;
+                Wp[m] = rt[k];
+                Akp[m] = A[k];
+                Amp[m] = A[M - k];
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < (kPre ? NP : 1); ++m)
+    for (int idx = threadIdx.x + m * 256; idx < R * H; idx += (kPre ? R * H : 256)) {
         const int q = idx >> LH, j = idx & (H - 1);
         const uint32_t col = column(j);
         const uint32_t t = col + (uint32_t)q * p;
@@ -545,10 +574,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
                 V oh; oh.x = (T)2 * Yh.x; oh.y = -(T)2 * Yh.y;
                 in[q * S] = oh;
             } else if (q < R / 2) {
-                spectral_pair_tk<T>(in[q * S], in[(R - q) * S], t, M, rt, A);
+                if (kPre) spectral_pair_vals<T>(in[q * S], in[(R - q) * S], t, M, Wp[m], Akp[m], Amp[m]);
+                else spectral_pair_tk<T>(in[q * S], in[(R - q) * S], t, M, rt, A);
             }
         } else {
-            spectral_pair_tk<T>(in[q * S + j], in[(R - 1 - q) * S + j + H], t, M, rt, A);
+            if (kPre) spectral_pair_vals<T>(in[q * S + j], in[(R - 1 - q) * S + j + H], t, M, Wp[m], Akp[m], Amp[m]);
+            else spectral_pair_tk<T>(in[q * S + j], in[(R - 1 - q) * S + j + H], t, M, rt, A);
         }
         if (ti == 0 && j == 0 && q < R / 2) {  // column p/2 pairs with itself
             spectral_pair_tk<T>(in[q * S + H], in[(R - 1 - q) * S + H], p / 2 + (uint32_t)q * p, M, rt, A);
