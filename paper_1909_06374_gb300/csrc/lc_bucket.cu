@@ -49,7 +49,7 @@ namespace lc {
 constexpr int kBkBuckets = 256;
 constexpr int kBkSample = 1024;
 constexpr int kBkSampleThreads = 128;
-constexpr int kBkThreads = 256;                  // finish kernel
+constexpr int kBkThreads = 512;                  // finish kernel: 4 elements per thread, 4 blocks per SM
 constexpr int kBkPer = kBkCap / kBkThreads;      // elements per finish thread
 constexpr int kBkTileThreads = 256;              // histogram and scatter kernels
 
@@ -674,7 +674,7 @@ static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort sc
 
 // One work-item slot per block (gmax slots per curve); a block whose slot is
 // empty returns at once.
-__global__ void __launch_bounds__(kBkThreads, 6) k_bk_finish(const BkArgs a)
+__global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
 {
     constexpr uint32_t kPosMask = (1u << 24) - 1u;
     const uint32_t item = blockIdx.x;
@@ -851,7 +851,7 @@ void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, v
     a.log2n = k.log2n;
     if (kt) kt->begin(kGroupSortHistScan, st);
     k_bk_sample<<<k.ncurves, kBkSampleThreads, 0, st>>>(a);
-    const int tpb = std::min(4, a.tpc);
+    const int tpb = std::min(2, a.tpc);  // two tiles per block: 32 registers, eight blocks per SM
     if (tpb >= 4) k_bk_hist<4><<<k.ncurves * (a.tpc / 4), kBkTileThreads, 0, st>>>(a);
     else if (tpb >= 2) k_bk_hist<2><<<k.ncurves * (a.tpc / 2), kBkTileThreads, 0, st>>>(a);
     else k_bk_hist<1><<<k.ncurves * a.tpc, kBkTileThreads, 0, st>>>(a);
