@@ -462,27 +462,45 @@ static lc_status run_setup(Plan& p, void* out_tk, cudaStream_t st, uint64_t* lau
         ++*launches;
     }
     for (auto& k : p.classes) { launch_erdf_draws<T>(p, k, st); *launches += (k.ntab < k.ncurves) + (k.ntab > 0); }
-    for (auto& k : p.classes) launch_sort<T>(p, k, p.d_x, kSortKeysToValues, false, st, launches);
+    {
+        // the draws of every class sorted with one launch per kernel form
+        std::vector<const ClassInfo*> ks;
+        for (auto& k : p.classes) ks.push_back(&k);
+        launch_sort<T>(p, ks, std::vector<const void*>(ks.size(), p.d_x), kSortKeysToValues, false, st, launches,
+                       nullptr, nullptr, false);
+    }
     cudaEventRecord(p.t_setup1, st);
     LC_CK(cudaGetLastError());
     p.setup_done = true;
     return LC_OK;
 }
 
-// One amplitude-adjustment iteration of every class (Sec. 3.2.2).
+// One amplitude-adjustment iteration of every class (Sec. 3.2.2).  Stage by
+// stage over the classes: the transforms of the tile-path classes with one
+// launch per kernel form and stage (launch_fft_iteration), those of the short
+// classes per class, then the rank-order step of all of them with one launch
+// per kernel form (launch_sort).  Classes touch disjoint parts of the plan's
+// buffers, so their kernels of one stage can share a launch.
 template <typename T>
 static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches, KernelTimes* kt = nullptr)
 {
+    // with the convergence test the FFTs work in d_f and d_keysB (free
+    // until the sort starts) so that x_{i-1} stays in d_x for Eq. 4
+    void* alt = p.conv_on ? p.d_keysB : p.d_x;
+    std::vector<const ClassInfo*> tile, multi;
+    for (auto& k : p.classes)
+        if (!k.resident && k.log2n - 1 >= 12) tile.push_back(&k);
+    if (kt) kt->begin(kGroupFFT, st);
+    std::vector<void*> tile_out;
+    if (!tile.empty()) launch_fft_iteration<T>(p, tile, p.d_x, p.d_f, alt, st, launches, tile_out);
+    std::vector<const void*> src;
+    size_t ti = 0;
     for (auto& k : p.classes) {
         if (k.resident) continue;
-        if (kt) kt->begin(kGroupFFT, st);
-        // with the convergence test the FFTs work in d_f and d_keysB (free
-        // until the sort starts) so that x_{i-1} stays in d_x for Eq. 4
-        void* alt = p.conv_on ? p.d_keysB : p.d_x;
         void* R3;
         if (k.log2n - 1 >= 12) {
             // tile path: the spectral step runs inside the transforms' middle passes
-            R3 = launch_fft_iteration<T>(p, k, p.d_x, p.d_f, alt, st, launches);
+            R3 = tile_out[ti++];
         } else {
             void* R1 = launch_fft<T>(p, k, false, p.d_x, p.d_f, nullptr, true, st, launches,
                                      p.conv_on ? p.d_keysB : nullptr);
@@ -491,19 +509,26 @@ static void enqueue_iteration(Plan& p, cudaStream_t st, uint64_t* launches, Kern
             ++*launches;
             R3 = launch_fft<T>(p, k, true, Zp, R1, nullptr, true, st, launches);
         }
-        if (kt) kt->end(st);
+        multi.push_back(&k);
+        src.push_back(R3);
+    }
+    if (kt) kt->end(st);
+    if (!multi.empty()) {
+        // the tile path's inverse transform has written the sample-sorted
+        // classes' samples of x_adj (presampled)
         if (!p.conv_on) {
-            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, nullptr, kt, k.log2n - 1 >= 12);
+            launch_sort<T>(p, multi, src, kSortArgsortScatter, true, st, launches, nullptr, kt, true);
         } else {
             // the last sort pass reads keys A, so x_i can go to keys B; Eq. 4
             // then compares it with x_{i-1} in one coalesced pass
-            launch_sort<T>(p, k, R3, kSortArgsortScatter, true, st, launches, p.d_keysB, kt,
-                           k.log2n - 1 >= 12);
+            launch_sort<T>(p, multi, src, kSortArgsortScatter, true, st, launches, p.d_keysB, kt, true);
             if (kt) kt->begin(kGroupOther, st);
-            launch_conv_delta<T>(p, k, p.d_keysB, st);
-            launch_conv_finalize(p, k, st);
+            for (const ClassInfo* k : multi) {
+                launch_conv_delta<T>(p, *k, p.d_keysB, st);
+                launch_conv_finalize(p, *k, st);
+                *launches += 2;
+            }
             if (kt) kt->end(st);
-            *launches += 2;
         }
     }
     launch_iter_increment(p, st);

@@ -199,11 +199,14 @@ __device__ __forceinline__ int cell_slot(int c)
 // 32 (8 w + i) + l in v[i], i < 8, so the stages with a partner distance j < 32
 // exchange through warp shuffles, those with j = 32, 64, 128 stay inside the
 // thread, and only j = 256 and 512 go through shared memory.
-__global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
+template <bool MULTI>
+__global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const __grid_constant__ LaunchSet<BkArgs> set)
 {
+    uint32_t blk;
+    const BkArgs& a = set.pick<MULTI>(blk);
     static_assert(kBkSample == 1024 && kBkSampleThreads == 128, "register layout of the sample sort");
     constexpr int PER = kBkSample / kBkSampleThreads;  // 8 elements per thread
-    const int ci = blockIdx.x;
+    const int ci = (int)blk;
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float sm[kBkSample];
@@ -313,13 +316,15 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const BkArgs a)
 // ------------------------------------------------------------------ histogram
 // TPB tiles per block: bucket counts per tile and the bucket of every element
 // (one byte, packed four to a word, for the scatter).
-template <int TPB>
-__global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
+template <int TPB, bool MULTI>
+__global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const __grid_constant__ LaunchSet<BkArgs> set)
 {
+    uint32_t blk;
+    const BkArgs& a = set.pick<MULTI>(blk);
     constexpr int V4 = kSortTile / 4 / kBkTileThreads;  // float4 loads per thread and tile
     const int bpc = a.tpc / TPB;
-    const int ci = blockIdx.x / bpc;
-    const int t0 = (blockIdx.x % bpc) * TPB;
+    const int ci = (int)blk / bpc;
+    const int t0 = ((int)blk % bpc) * TPB;
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float spl[kBkBuckets];
@@ -370,10 +375,13 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const BkArgs a)
 // group of its own), found for every s at once by binary search; thread 0
 // then follows these links from bucket 0.  Any two consecutive groups hold
 // more than kBkCap elements, so a curve has at most gmax = 2 N / kBkCap + 1.
-__global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
+template <bool MULTI>
+__global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const __grid_constant__ LaunchSet<BkArgs> set)
 {
+    uint32_t blk;
+    const BkArgs& a = set.pick<MULTI>(blk);
     constexpr int kChunk = 32;  // tile counts loaded together
-    const int ci = blockIdx.x;
+    const int ci = (int)blk;
     const int c = a.cls_curves[ci];
     uint4* items = a.items + 2 * (size_t)ci * a.gmax;
     if (!bk_active(a, c)) {
@@ -473,11 +481,14 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const BkArgs a)
 // order (slot atomics: the order inside a bucket is arbitrary), then each
 // bucket's run is written to the tile's slice of the bucket with coalesced
 // stores.
-__global__ void __launch_bounds__(kBkTileThreads) k_bk_scatter(const BkArgs a)
+template <bool MULTI>
+__global__ void __launch_bounds__(kBkTileThreads) k_bk_scatter(const __grid_constant__ LaunchSet<BkArgs> set)
 {
+    uint32_t blk;
+    const BkArgs& a = set.pick<MULTI>(blk);
     constexpr int V4 = kSortTile / 4 / kBkTileThreads;
-    const int ci = blockIdx.x / a.tpc;
-    const int t = blockIdx.x % a.tpc;
+    const int ci = (int)blk / a.tpc;
+    const int t = (int)blk % a.tpc;
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
     __shared__ float stk[kSortTile];
@@ -674,10 +685,13 @@ static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort sc
 
 // One work-item slot per block (gmax slots per curve); a block whose slot is
 // empty returns at once.
-__global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const BkArgs a)
+template <bool MULTI>
+__global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_constant__ LaunchSet<BkArgs> set)
 {
+    uint32_t blk;
+    const BkArgs& a = set.pick<MULTI>(blk);
     constexpr uint32_t kPosMask = (1u << 24) - 1u;
-    const uint32_t item = blockIdx.x;
+    const uint32_t item = blk;
     const uint4 d0 = a.items[2 * item];
     const uint4 d1 = a.items[2 * item + 1];
     const uint32_t e0 = d0.x, b0 = d0.z;
@@ -823,45 +837,99 @@ constexpr size_t kBkFinishSmem = (size_t)kFinWords * 4;
 
 cudaError_t bucket_kernel_attributes()
 {
-    return cudaFuncSetAttribute(k_bk_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBkFinishSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_bk_finish<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kBkFinishSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bk_finish<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBkFinishSmem);
+    return e;
+}
+
+template <int TPB>
+static int launch_hist_sets(const std::vector<BkArgs>& args, const std::vector<uint32_t>& blocks, cudaStream_t st)
+{
+    return for_launch_sets(args, blocks, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_hist<TPB, true><<<g, kBkTileThreads, 0, st>>>(s);
+        else k_bk_hist<TPB, false><<<g, kBkTileThreads, 0, st>>>(s);
+    });
+}
+
+void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& ks,
+                           const std::vector<const void*>& srcs, void* x_out, bool gated, bool presampled,
+                           cudaStream_t st, uint64_t* launches, KernelTimes* kt)
+{
+    const size_t nk = ks.size();
+    std::vector<BkArgs> args(nk);
+    std::vector<uint32_t> b_curve(nk), b_tile(nk), b_item(nk);
+    // histogram blocks: two tiles per block (32 registers, eight blocks per
+    // SM) where the curve has them
+    std::vector<BkArgs> h1, h2;
+    std::vector<uint32_t> hb1, hb2;
+    for (size_t i = 0; i < nk; ++i) {
+        const ClassInfo& k = *ks[i];
+        BkArgs& a = args[i];
+        a = BkArgs{};
+        // only the tile path's inverse transform (log2 N >= 13) writes the sample
+        a.presampled = (presampled && k.log2n - 1 >= 12) ? 1 : 0;
+        a.cls_curves = k.d_curves;
+        a.curves = p.d_curves;
+        a.eff_iters = p.d_eff_iters;
+        a.d_iter = gated ? p.d_iter : nullptr;
+        a.xadj = (const float*)srcs[i];
+        a.aux = k.d_aux + kAuxHeader;
+        a.items = (uint4*)(k.d_aux + kAuxHeader + (size_t)k.ncurves * kAuxCurveWords);
+        a.hist = p.d_hist + k.hist_off;
+        a.bid = p.d_valsB;  // free until the finish: the bucket bytes of curve c at word off_c
+        a.keys = (uint32_t*)p.d_keysA;
+        a.vals = p.d_valsA;
+        a.keys2 = (uint32_t*)p.d_f;
+        a.vals2 = p.d_valsB;
+        a.s = (const float*)p.d_s;
+        a.x_out = (float*)(x_out ? x_out : p.d_x);
+        a.tpc = k.tiles_per_curve;
+        a.gmax = bucket_gmax(k.log2n);
+        a.log2n = k.log2n;
+        b_curve[i] = (uint32_t)k.ncurves;
+        b_tile[i] = (uint32_t)(k.ncurves * a.tpc);
+        b_item[i] = (uint32_t)(k.ncurves * a.gmax);
+        if (a.tpc >= 2) {
+            h2.push_back(a);
+            hb2.push_back((uint32_t)(k.ncurves * (a.tpc / 2)));
+        } else {
+            h1.push_back(a);
+            hb1.push_back((uint32_t)(k.ncurves * a.tpc));
+        }
+    }
+    int n = 0;
+    if (kt) kt->begin(kGroupSortHistScan, st);
+    n += for_launch_sets(args, b_curve, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_sample<true><<<g, kBkSampleThreads, 0, st>>>(s);
+        else k_bk_sample<false><<<g, kBkSampleThreads, 0, st>>>(s);
+    });
+    n += launch_hist_sets<2>(h2, hb2, st);
+    n += launch_hist_sets<1>(h1, hb1, st);
+    n += for_launch_sets(args, b_curve, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_scan<true><<<g, kBkBuckets, 0, st>>>(s);
+        else k_bk_scan<false><<<g, kBkBuckets, 0, st>>>(s);
+    });
+    if (kt) kt->end(st);
+    if (kt) kt->begin(kGroupSortScatter, st);
+    n += for_launch_sets(args, b_tile, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_scatter<true><<<g, kBkTileThreads, 0, st>>>(s);
+        else k_bk_scatter<false><<<g, kBkTileThreads, 0, st>>>(s);
+    });
+    n += for_launch_sets(args, b_item, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_finish<true><<<g, kBkThreads, kBkFinishSmem, st>>>(s);
+        else k_bk_finish<false><<<g, kBkThreads, kBkFinishSmem, st>>>(s);
+    });
+    if (kt) kt->end(st);
+    if (launches) *launches += (uint64_t)n;
 }
 
 void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, void* x_out, bool gated,
                            bool presampled, cudaStream_t st, uint64_t* launches, KernelTimes* kt)
 {
-    BkArgs a{};
-    a.presampled = presampled ? 1 : 0;
-    a.cls_curves = k.d_curves;
-    a.curves = p.d_curves;
-    a.eff_iters = p.d_eff_iters;
-    a.d_iter = gated ? p.d_iter : nullptr;
-    a.xadj = (const float*)src;
-    a.aux = k.d_aux + kAuxHeader;
-    a.items = (uint4*)(k.d_aux + kAuxHeader + (size_t)k.ncurves * kAuxCurveWords);
-    a.hist = p.d_hist + k.hist_off;
-    a.bid = p.d_valsB;  // free until the finish: the bucket bytes of curve c at word off_c
-    a.keys = (uint32_t*)p.d_keysA;
-    a.vals = p.d_valsA;
-    a.keys2 = (uint32_t*)p.d_f;
-    a.vals2 = p.d_valsB;
-    a.s = (const float*)p.d_s;
-    a.x_out = (float*)(x_out ? x_out : p.d_x);
-    a.tpc = k.tiles_per_curve;
-    a.gmax = bucket_gmax(k.log2n);
-    a.log2n = k.log2n;
-    if (kt) kt->begin(kGroupSortHistScan, st);
-    k_bk_sample<<<k.ncurves, kBkSampleThreads, 0, st>>>(a);
-    const int tpb = std::min(2, a.tpc);  // two tiles per block: 32 registers, eight blocks per SM
-    if (tpb >= 4) k_bk_hist<4><<<k.ncurves * (a.tpc / 4), kBkTileThreads, 0, st>>>(a);
-    else if (tpb >= 2) k_bk_hist<2><<<k.ncurves * (a.tpc / 2), kBkTileThreads, 0, st>>>(a);
-    else k_bk_hist<1><<<k.ncurves * a.tpc, kBkTileThreads, 0, st>>>(a);
-    k_bk_scan<<<k.ncurves, kBkBuckets, 0, st>>>(a);
-    if (kt) kt->end(st);
-    if (kt) kt->begin(kGroupSortScatter, st);
-    k_bk_scatter<<<k.ncurves * a.tpc, kBkTileThreads, 0, st>>>(a);
-    k_bk_finish<<<(unsigned)(k.ncurves * a.gmax), kBkThreads, kBkFinishSmem, st>>>(a);
-    if (kt) kt->end(st);
-    if (launches) *launches += 5;
+    launch_bucket_argsort(p, std::vector<const ClassInfo*>{&k}, std::vector<const void*>{src}, x_out, gated,
+                          presampled, st, launches, kt);
 }
 
 }  // namespace lc

@@ -239,9 +239,12 @@ __device__ __forceinline__ void tile_dft(cplx<T>* __restrict__ buf, const SmemTw
     }
 }
 
-template <typename T, int LR, bool INV>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft_tile(const PassArgs a)
+template <typename T, int LR, bool INV, bool MULTI>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2)
+    k_fft_tile(const __grid_constant__ LaunchSet<PassArgs> set)
 {
+    uint32_t blk;
+    const PassArgs& a = set.pick<MULTI>(blk);
     using V = cplx<T>;
     constexpr int R = 1 << LR;
     constexpr int C = tile_cols(LR, (int)sizeof(V));
@@ -252,8 +255,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     V* twm = b0 + R * S;
     const uint32_t log2nb = a.log2M - LR;
     const int tpc = 1 << (log2nb - LC);      // tiles per curve (nb >= C)
-    const int ci = blockIdx.x / tpc;
-    const int ti = blockIdx.x % tpc;
+    const int ci = (int)blk / tpc;
+    const int ti = (int)blk % tpc;
     const int c = a.cls_curves[ci];
     if (a.d_iter && (uint32_t)(*a.d_iter) >= a.eff_iters[c]) return;
     const uint64_t base = a.curves[c].off >> 1;
@@ -484,9 +487,12 @@ __device__ __forceinline__ void spectral_pair_tk(cplx<T>& za, cplx<T>& zb, uint3
 // and their H partner columns -- column pairs (0, p/2), then (g, p - g) -- so
 // all three steps stay in shared memory, saving two passes over the spectrum
 // and the spectral kernel.  Output: y[i R + q] for the block's columns i.
-template <typename T, int LR>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft_spectral(const PassArgs a, const void* __restrict__ A_all)
+template <typename T, int LR, bool MULTI>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2)
+    k_fft_spectral(const __grid_constant__ LaunchSet<PassArgs> set, const void* __restrict__ A_all)
 {
+    uint32_t blk;
+    const PassArgs& a = set.pick<MULTI>(blk);
     using V = cplx<T>;
     constexpr int R = 1 << LR;
     constexpr int C = tile_cols(LR, (int)sizeof(V));
@@ -500,8 +506,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && LR < 9) ? 4 : 2) k_fft
     const uint32_t log2p = a.log2M - LR;
     const uint32_t p = 1u << log2p;  // indices within a curve: 32-bit (M <= 2^26)
     const int tpc = (int)(p >> LC);
-    const int ci = blockIdx.x / tpc;
-    const int ti = blockIdx.x % tpc;
+    const int ci = (int)blk / tpc;
+    const int ti = (int)blk % tpc;
     const int c = a.cls_curves[ci];
     if (a.d_iter && (uint32_t)(*a.d_iter) >= a.eff_iters[c]) return;
     const CurveDev& cv = a.curves[c];
@@ -688,15 +694,24 @@ static size_t tile_smem_bytes(int LR, int log2M)
 // The longest transform of the tile path: M = 2^26 (N = 2^27).
 constexpr int kTileMaxLog2M = 26;
 
+template <typename T, int LR, bool MULTI>
+static cudaError_t tile_attrs_m(int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fft_tile<T, LR, false, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_tile<T, LR, true, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_spectral<T, LR, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 template <typename T, int LR>
 static cudaError_t tile_attrs()
 {
     const int smem = (int)tile_smem_bytes<T>(LR, kTileMaxLog2M);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_tile<T, LR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_tile<T, LR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_spectral<T, LR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = tile_attrs_m<T, LR, false>(smem);
+    if (e == cudaSuccess) e = tile_attrs_m<T, LR, true>(smem);
     return e;
 }
 
@@ -720,23 +735,66 @@ cudaError_t fft_kernel_attributes()
     return e;
 }
 
+// One tile pass of radix 2^LR over the launch set's classes; dynamic shared
+// memory for the longest of them.
 template <typename T, int LR, bool INV>
-static void launch_tile_lr(const PassArgs& a, int blocks, cudaStream_t st)
+static void launch_tile_lr(const LaunchSet<PassArgs>& s, uint32_t blocks, size_t smem, bool multi, cudaStream_t st)
 {
-    k_fft_tile<T, LR, INV><<<blocks, 256, tile_smem_bytes<T>(LR, (int)a.log2M), st>>>(a);
+    if (multi) k_fft_tile<T, LR, INV, true><<<blocks, 256, smem, st>>>(s);
+    else k_fft_tile<T, LR, INV, false><<<blocks, 256, smem, st>>>(s);
+}
+
+template <typename T, bool INV>
+static void launch_tile_set(int LR, const LaunchSet<PassArgs>& s, uint32_t blocks, bool multi, cudaStream_t st)
+{
+    size_t smem = 0;
+    for (int i = 0; i < s.n; ++i) smem = std::max(smem, tile_smem_bytes<T>(LR, (int)s.c[i].log2M));
+    switch (LR) {
+    case 5: launch_tile_lr<T, 5, INV>(s, blocks, smem, multi, st); break;
+    case 6: launch_tile_lr<T, 6, INV>(s, blocks, smem, multi, st); break;
+    case 7: launch_tile_lr<T, 7, INV>(s, blocks, smem, multi, st); break;
+    case 8: launch_tile_lr<T, 8, INV>(s, blocks, smem, multi, st); break;
+    default:
+        if (sizeof(T) == 4 && LR == 9) launch_tile_lr<float, 9, INV>(s, blocks, smem, multi, st);
+        else set_error("internal: unsupported tile radix");
+        break;
+    }
 }
 
 template <typename T, bool INV>
 static void launch_tile(int LR, const PassArgs& a, int blocks, cudaStream_t st)
 {
+    LaunchSet<PassArgs> s{};
+    s.c[0] = a;
+    s.n = 1;
+    launch_tile_set<T, INV>(LR, s, (uint32_t)blocks, false, st);
+}
+
+// The fused spectral kernel of radix 2^LR over the launch set's classes.
+template <typename T>
+static void launch_spectral_set(int LR, const LaunchSet<PassArgs>& s, uint32_t blocks, bool multi, const void* A,
+                                cudaStream_t st)
+{
+    size_t smem = 0;
+    for (int i = 0; i < s.n; ++i) smem = std::max(smem, tile_smem_bytes<T>(LR, (int)s.c[i].log2M));
     switch (LR) {
-    case 5: launch_tile_lr<T, 5, INV>(a, blocks, st); break;
-    case 6: launch_tile_lr<T, 6, INV>(a, blocks, st); break;
-    case 7: launch_tile_lr<T, 7, INV>(a, blocks, st); break;
-    case 8: launch_tile_lr<T, 8, INV>(a, blocks, st); break;
+#define LC_FUSED_CASE(L)                                                               \
+    case L:                                                                            \
+        if (multi) k_fft_spectral<T, L, true><<<blocks, 256, smem, st>>>(s, A);         \
+        else k_fft_spectral<T, L, false><<<blocks, 256, smem, st>>>(s, A);              \
+        break;
+        LC_FUSED_CASE(5)
+        LC_FUSED_CASE(6)
+        LC_FUSED_CASE(7)
+        LC_FUSED_CASE(8)
+#undef LC_FUSED_CASE
     default:
-        if (sizeof(T) == 4 && LR == 9) launch_tile_lr<float, 9, INV>(a, blocks, st);
-        else set_error("internal: unsupported tile radix");
+        if (sizeof(T) == 4 && LR == 9) {
+            if (multi) k_fft_spectral<float, 9, true><<<blocks, 256, smem, st>>>(s, A);
+            else k_fft_spectral<float, 9, false><<<blocks, 256, smem, st>>>(s, A);
+        } else {
+            set_error("internal: unsupported fused radix");
+        }
         break;
     }
 }
@@ -823,75 +881,133 @@ void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_
 }
 
 // Forward transform, spectral step and inverse transform of one iteration
-// on the tile path (log2 M >= 12): the forward passes but the last, the fused
-// k_fft_spectral, then the inverse passes in reverse radix order.  Buffers:
-// `in` is read by the first pass only; the passes alternate between b and c
-// (c may be `in` itself).  Returns the buffer with x_adj.
+// on the tile path (log2 M >= 12) for several classes at once: the forward
+// passes but the last, the fused k_fft_spectral, then the inverse passes in
+// reverse radix order.  Stage by stage, each kernel form (tile pass or fused
+// kernel, radix) is launched once for every class that takes it at that
+// stage; forward pass f of every class runs in stage f, and the inverse
+// passes are aligned on the last one (which also writes the sample-sorted
+// classes' sample of x_adj).  Buffers: `in` is read by the first pass only;
+// the passes alternate between b and c (c may be `in` itself).  outs[i]
+// receives the buffer with class i's x_adj.
+template <typename T>
+void launch_fft_iteration(const Plan& p, const std::vector<const ClassInfo*>& ks, void* in, void* b, void* c,
+                          cudaStream_t st, uint64_t* launches, std::vector<void*>& outs)
+{
+    struct ClassState {
+        const ClassInfo* k;
+        PassArgs a;
+        std::vector<int> lr;
+        int P;
+        void* cur;
+        void* nxt;
+        uint32_t log2p;
+    };
+    const size_t nk = ks.size();
+    std::vector<ClassState> cs(nk);
+    int maxf = 0;
+    for (size_t i = 0; i < nk; ++i) {
+        ClassState& x = cs[i];
+        x.k = ks[i];
+        x.a = PassArgs{};
+        x.a.cls_curves = x.k->d_curves;
+        x.a.curves = p.d_curves;
+        x.a.eff_iters = p.d_eff_iters;
+        x.a.d_iter = p.d_iter;
+        x.a.tw = x.k->d_tw;
+        x.a.ncurves = x.k->ncurves;
+        x.a.log2M = x.k->log2n - 1;
+        x.lr = tile_radices(x.a.log2M, sizeof(T) == 8);
+        x.P = (int)x.lr.size();
+        x.cur = in;
+        x.nxt = b;
+        x.log2p = 0;
+        maxf = std::max(maxf, x.P - 1);
+    }
+    auto step = [&](ClassState& x) {
+        void* w = x.nxt;
+        x.nxt = (w == b) ? c : b;
+        x.cur = w;
+    };
+    // (class, radix) pairs of one stage, launched grouped by radix
+    std::vector<std::pair<int, int>> sel;
+    auto stage = [&](int kind) {  // 0: forward tile pass, 1: fused spectral kernel, 2: inverse tile pass
+        for (int LR = 5; LR <= 9; ++LR) {
+            std::vector<PassArgs> args;
+            std::vector<uint32_t> blocks;
+            for (const auto& e : sel) {
+                if (e.second != LR) continue;
+                const ClassState& x = cs[e.first];
+                args.push_back(x.a);
+                blocks.push_back((uint32_t)tile_blocks<T>(x.k->ncurves, x.a.log2M, LR));
+            }
+            if (args.empty()) continue;
+            const int n = for_launch_sets(args, blocks, [&](const LaunchSet<PassArgs>& s, uint32_t g, bool multi) {
+                if (kind == 0) launch_tile_set<T, false>(LR, s, g, multi, st);
+                else if (kind == 1) launch_spectral_set<T>(LR, s, g, multi, p.d_A, st);
+                else launch_tile_set<T, true>(LR, s, g, multi, st);
+            });
+            if (launches) *launches += (uint64_t)n;
+        }
+    };
+    for (int f = 0; f < maxf; ++f) {
+        sel.clear();
+        for (size_t i = 0; i < nk; ++i) {
+            ClassState& x = cs[i];
+            if (f >= x.P - 1) continue;
+            x.a.in = x.cur; x.a.out = x.nxt; x.a.log2p = x.log2p;
+            sel.emplace_back((int)i, x.lr[f]);
+        }
+        stage(0);
+        for (const auto& e : sel) {
+            ClassState& x = cs[e.first];
+            x.log2p += (uint32_t)x.lr[f];
+            step(x);
+        }
+    }
+    sel.clear();
+    for (size_t i = 0; i < nk; ++i) {
+        ClassState& x = cs[i];
+        x.a.in = x.cur; x.a.out = x.nxt; x.a.log2p = x.log2p;
+        sel.emplace_back((int)i, x.lr[x.P - 1]);
+    }
+    stage(1);
+    for (size_t i = 0; i < nk; ++i) {
+        ClassState& x = cs[i];
+        step(x);
+        x.log2p = (uint32_t)x.lr[x.P - 1];
+    }
+    for (int r = maxf - 1; r >= 0; --r) {
+        sel.clear();
+        for (size_t i = 0; i < nk; ++i) {
+            ClassState& x = cs[i];
+            if (r > x.P - 2) continue;
+            x.a.in = x.cur; x.a.out = x.nxt; x.a.log2p = x.log2p;
+            if (r == 0 && x.k->bucket && sizeof(T) == 4) {  // the sample sort's sample of x_adj
+                x.a.smp = bucket_sample_area(*x.k);
+                x.a.smp_words = (uint32_t)bucket_curve_words();
+                x.a.smp_shift = bucket_sample_shift(x.k->log2n);
+            }
+            sel.emplace_back((int)i, x.lr[r]);
+        }
+        stage(2);
+        for (const auto& e : sel) {
+            ClassState& x = cs[e.first];
+            x.log2p += (uint32_t)x.lr[r];
+            step(x);
+        }
+    }
+    outs.assign(nk, nullptr);
+    for (size_t i = 0; i < nk; ++i) outs[i] = cs[i].cur;
+}
+
 template <typename T>
 void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b, void* c, cudaStream_t st,
                            uint64_t* launches)
 {
-    PassArgs a{};
-    a.cls_curves = k.d_curves;
-    a.curves = p.d_curves;
-    a.eff_iters = p.d_eff_iters;
-    a.d_iter = p.d_iter;
-    a.tw = k.d_tw;
-    a.ncurves = k.ncurves;
-    a.log2M = k.log2n - 1;
-    const std::vector<int> lr = tile_radices(a.log2M, sizeof(T) == 8);
-    const int P = (int)lr.size();
-    void* cur = in;
-    void* nxt = b;
-    auto step = [&]() { void* w = nxt; nxt = (w == b) ? c : b; cur = w; };
-    uint32_t log2p = 0;
-    for (int q = 0; q + 1 < P; ++q) {
-        a.in = cur; a.out = nxt; a.log2p = log2p;
-        launch_tile<T, false>(lr[q], a, tile_blocks<T>(k.ncurves, a.log2M, lr[q]), st);
-        if (launches) ++*launches;
-        log2p += (uint32_t)lr[q];
-        step();
-    }
-    const int LR = lr[P - 1];
-    a.in = cur; a.out = nxt; a.log2p = log2p;
-    {
-        const int blocks = tile_blocks<T>(k.ncurves, a.log2M, LR);
-        const size_t smem = tile_smem_bytes<T>(LR, (int)a.log2M);
-        switch (LR) {
-#define LC_FUSED_CASE(L)                                            \
-    case L:                                                         \
-        k_fft_spectral<T, L><<<blocks, 256, smem, st>>>(a, p.d_A); \
-        break;
-            LC_FUSED_CASE(5)
-            LC_FUSED_CASE(6)
-            LC_FUSED_CASE(7)
-            LC_FUSED_CASE(8)
-#undef LC_FUSED_CASE
-        default:
-            if (sizeof(T) == 4 && LR == 9) {
-                k_fft_spectral<float, 9><<<blocks, 256, smem, st>>>(a, p.d_A);
-            } else {
-                set_error("internal: unsupported fused radix");
-            }
-            break;
-        }
-        if (launches) ++*launches;
-    }
-    step();
-    log2p = (uint32_t)LR;
-    for (int q = P - 2; q >= 0; --q) {
-        a.in = cur; a.out = nxt; a.log2p = log2p;
-        if (q == 0 && k.bucket && sizeof(T) == 4) {  // the sample sort's sample of x_adj
-            a.smp = bucket_sample_area(k);
-            a.smp_words = (uint32_t)bucket_curve_words();
-            a.smp_shift = bucket_sample_shift(k.log2n);
-        }
-        launch_tile<T, true>(lr[q], a, tile_blocks<T>(k.ncurves, a.log2M, lr[q]), st);
-        if (launches) ++*launches;
-        log2p += (uint32_t)lr[q];
-        step();
-    }
-    return cur;
+    std::vector<void*> outs;
+    launch_fft_iteration<T>(p, std::vector<const ClassInfo*>{&k}, in, b, c, st, launches, outs);
+    return outs[0];
 }
 
 template void launch_twiddles<float>(const ClassInfo&, cudaStream_t);
@@ -904,6 +1020,10 @@ template void* launch_fft_iteration<float>(const Plan&, const ClassInfo&, void*,
                                            uint64_t*);
 template void* launch_fft_iteration<double>(const Plan&, const ClassInfo&, void*, void*, void*, cudaStream_t,
                                             uint64_t*);
+template void launch_fft_iteration<float>(const Plan&, const std::vector<const ClassInfo*>&, void*, void*, void*,
+                                          cudaStream_t, uint64_t*, std::vector<void*>&);
+template void launch_fft_iteration<double>(const Plan&, const std::vector<const ClassInfo*>&, void*, void*, void*,
+                                           cudaStream_t, uint64_t*, std::vector<void*>&);
 template void launch_spectral_iter<float>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
 template void launch_spectral_iter<double>(const Plan&, const ClassInfo&, const void*, void*, cudaStream_t);
 template void launch_spectral_tk<float>(const Plan&, const ClassInfo&, void*, cudaStream_t);

@@ -132,6 +132,62 @@ struct KernelTimes {
 // ConvDev of a plan: null pointers when the convergence test is off.
 inline ConvDev conv_of(const Plan& p) { return p.conv_on ? p.conv : ConvDev{}; }
 
+// One launch of a stage's kernel over up to kSetMax length classes: entry k
+// (its own kernel arguments c[k]) owns blocks [start[k], start[k + 1]) of
+// the grid, start[0] = 0.  Kernels take it as a __grid_constant__ parameter
+// and have two forms: MULTI = false (one entry; c[0] is read at fixed
+// offsets of the parameter space and the block index is blockIdx.x) and
+// MULTI = true (the entry is found by comparing blockIdx.x with start[]).
+// Both forms run the same per-block code, so a curve's results do not
+// depend on the classes it is launched with.
+constexpr int kSetMax = 8;
+template <class A>
+struct LaunchSet {
+    A c[kSetMax];
+    uint32_t start[kSetMax];
+    int n;
+#ifdef __CUDACC__
+    template <bool MULTI>
+    __device__ __forceinline__ const A& pick(uint32_t& bid) const
+    {
+        if (!MULTI) {
+            bid = blockIdx.x;
+            return c[0];
+        }
+        int k = 0;
+#pragma unroll
+        for (int i = 1; i < kSetMax; ++i) k += (i < n && blockIdx.x >= start[i]) ? 1 : 0;
+        bid = blockIdx.x - start[k];
+        return c[k];
+    }
+#endif
+};
+
+// Splits (args[i], blocks[i]) into launch sets of at most kSetMax entries
+// (entries with no blocks are left out) and calls go(set, grid blocks,
+// multi) for each; returns the number of launches.
+template <class A, class F>
+int for_launch_sets(const std::vector<A>& args, const std::vector<uint32_t>& blocks, F&& go)
+{
+    int launches = 0;
+    size_t i = 0;
+    while (i < args.size()) {
+        LaunchSet<A> s{};
+        uint32_t total = 0;
+        for (; i < args.size() && s.n < kSetMax; ++i) {
+            if (blocks[i] == 0) continue;
+            s.c[s.n] = args[i];
+            s.start[s.n] = total;
+            total += blocks[i];
+            ++s.n;
+        }
+        if (s.n == 0) continue;
+        go(s, total, s.n > 1);
+        ++launches;
+    }
+    return launches;
+}
+
 // lags of one lc_structure_function call
 constexpr size_t kMaxLags = 4096;
 
@@ -167,6 +223,11 @@ template <typename T> void launch_spectral_iter(const Plan& p, const ClassInfo& 
 // b and c (c may be in); returns the buffer holding x_adj.  Gated.
 template <typename T> void* launch_fft_iteration(const Plan& p, const ClassInfo& k, void* in, void* b, void* c,
                                                  cudaStream_t st, uint64_t* launches);
+// The same for several tile-path classes, stage by stage with one launch per
+// kernel form of a stage; outs[i] receives the buffer with ks[i]'s x_adj.
+template <typename T> void launch_fft_iteration(const Plan& p, const std::vector<const ClassInfo*>& ks, void* in,
+                                                void* b, void* c, cudaStream_t st, uint64_t* launches,
+                                                std::vector<void*>& outs);
 template <typename T> void launch_spectral_tk(const Plan& p, const ClassInfo& k, void* Zp, cudaStream_t st);
 
 // sort stage (lc_sort.cu)
@@ -181,6 +242,12 @@ enum SortMode { kSortArgsortScatter = 1, kSortKeysToValues = 2 };
 template <typename T> void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode,
                                        bool gated, cudaStream_t st, uint64_t* launches, void* x_out = nullptr,
                                        KernelTimes* kt = nullptr, bool presampled = false);
+// The same for several classes (srcs[i]: the values of ks[i]): each kernel of
+// a pass is launched once for all classes that share its form.
+template <typename T> void launch_sort(const Plan& p, const std::vector<const ClassInfo*>& ks,
+                                       const std::vector<const void*>& srcs, SortMode mode, bool gated,
+                                       cudaStream_t st, uint64_t* launches, void* x_out, KernelTimes* kt,
+                                       bool presampled);
 // sample-sort argsort of the iteration (lc_bucket.cu): FP32 curves of
 // 2^kBkMinLog2 .. 2^kBkMaxLog2 samples (256 buckets of N/256 elements on
 // average); groups of at most kBkCap elements are ranked in shared memory
@@ -196,6 +263,11 @@ cudaError_t bucket_kernel_attributes();
 // x_out[perm[r]] = s[r] with perm the stable argsort of `src` (gated).
 void launch_bucket_argsort(const Plan& p, const ClassInfo& k, const void* src, void* x_out, bool gated,
                            bool presampled, cudaStream_t st, uint64_t* launches, KernelTimes* kt);
+// The same for several sample-sorted classes (srcs[i]: the values of
+// ks[i]) with one launch per kernel for all of them.
+void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& ks,
+                           const std::vector<const void*>& srcs, void* x_out, bool gated, bool presampled,
+                           cudaStream_t st, uint64_t* launches, KernelTimes* kt);
 // where the inverse transform's last pass writes the class's samples of
 // x_adj (curve ci at + ci bucket_curve_words() floats), and the shift of
 // their complex index (PassArgs::smp_shift)

@@ -88,15 +88,17 @@ __device__ __forceinline__ void scan_curve(const SortArgs& a, int ci, uint32_t* 
 // Per-tile 8-bit digit histograms of TPB consecutive tiles of one curve per
 // block: 16-byte loads, all of a thread's loads in flight before the
 // counting, per-warp counters.
-template <typename T, bool FIRST, int TPB>
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const SortArgs a)
+template <typename T, bool FIRST, int TPB, bool MULTI>
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const __grid_constant__ LaunchSet<SortArgs> set)
 {
+    uint32_t blk;
+    const SortArgs& a = set.pick<MULTI>(blk);
     using K = typename key_of<T>::type;
     constexpr int EPV = 16 / (int)sizeof(K);                  // keys per 16-byte load
     constexpr int VPT = kSortTile / EPV / kSortThreads;       // loads per thread and full tile
     const int bpc = a.tpc / TPB;                              // blocks per curve
-    const int ci = blockIdx.x / bpc;
-    const int t0 = (blockIdx.x % bpc) * TPB;
+    const int ci = (int)blk / bpc;
+    const int t0 = ((int)blk % bpc) * TPB;
     const int c = a.cls_curves[ci];
     if (!curve_active(a, c)) return;
     __shared__ uint32_t h[TPB][kSortWarps][256];
@@ -140,9 +142,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const SortArgs a)
 // One block per curve of at most kScanChunk tiles: the histograms become tile
 // prefixes and the digit bases go to cbase (k_sort_scan_tiles and
 // k_sort_scan_chunks in one launch).
-__global__ void __launch_bounds__(256) k_sort_scan_curve(const SortArgs a)
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_sort_scan_curve(const __grid_constant__ LaunchSet<SortArgs> set)
 {
-    const int ci = blockIdx.x;
+    uint32_t blk;
+    const SortArgs& a = set.pick<MULTI>(blk);
+    const int ci = (int)blk;
     if (!curve_active(a, a.cls_curves[ci])) return;
     __shared__ uint32_t wsum[kSortWarps];
     scan_curve(a, ci, wsum);
@@ -150,10 +155,13 @@ __global__ void __launch_bounds__(256) k_sort_scan_curve(const SortArgs a)
 
 // Exclusive prefix of every digit over the tiles of one chunk (in place) and
 // the chunk totals.
-__global__ void __launch_bounds__(256) k_sort_scan_tiles(const SortArgs a)
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_sort_scan_tiles(const __grid_constant__ LaunchSet<SortArgs> set)
 {
-    const int ci = blockIdx.x / a.nchunks;
-    const int ch = blockIdx.x % a.nchunks;
+    uint32_t blk;
+    const SortArgs& a = set.pick<MULTI>(blk);
+    const int ci = (int)blk / a.nchunks;
+    const int ch = (int)blk % a.nchunks;
     const int c = a.cls_curves[ci];
     if (!curve_active(a, c)) return;
     const int d = threadIdx.x;
@@ -173,9 +181,12 @@ __global__ void __launch_bounds__(256) k_sort_scan_tiles(const SortArgs a)
 }
 
 // Chunk prefixes, digit totals and the digit bases of one curve.
-__global__ void __launch_bounds__(256) k_sort_scan_chunks(const SortArgs a)
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_sort_scan_chunks(const __grid_constant__ LaunchSet<SortArgs> set)
 {
-    const int ci = blockIdx.x;
+    uint32_t blk;
+    const SortArgs& a = set.pick<MULTI>(blk);
+    const int ci = (int)blk;
     const int c = a.cls_curves[ci];
     if (!curve_active(a, c)) return;
     const int d = threadIdx.x;
@@ -359,14 +370,16 @@ __device__ __forceinline__ void sort_tile(const SortArgs& a, const T* __restrict
 
 // One pass over one tile per block: the tile's output bases come from the
 // per-tile histograms and their scan.
-template <typename T, bool FIRST, int MODE, int THREADS, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) k_sort_scatter(const SortArgs a)
+template <typename T, bool FIRST, int MODE, int THREADS, int MINB, bool MULTI>
+__global__ void __launch_bounds__(THREADS, MINB) k_sort_scatter(const __grid_constant__ LaunchSet<SortArgs> set)
 {
+    uint32_t blk;
+    const SortArgs& a = set.pick<MULTI>(blk);
     static_assert(THREADS >= 256 && THREADS % 256 == 0, "the per-digit steps take one thread per digit");
     using K = typename key_of<T>::type;
     constexpr int WARPS = THREADS / 32;
-    const int ci = blockIdx.x / a.tpc;
-    const int t = blockIdx.x % a.tpc;
+    const int ci = (int)blk / a.tpc;
+    const int t = (int)blk % a.tpc;
     const int c = a.cls_curves[ci];
     if (!curve_active(a, c)) return;
     __shared__ K sk[kSortTile];
@@ -493,98 +506,172 @@ void launch_conv_reset(const Plan& p, cudaStream_t st)
     k_conv_reset<<<blocks, 256, 0, st>>>(p.conv.delta, n);
 }
 
-template <typename T, bool FIRST, int THREADS, int MINB>
-static void launch_scatter_v(int mode, const SortArgs& a, int blocks, cudaStream_t st)
-{
-    if (mode == 0) k_sort_scatter<T, FIRST, 0, THREADS, MINB><<<blocks, THREADS, 0, st>>>(a);
-    else if (mode == kSortArgsortScatter) k_sort_scatter<T, FIRST, kSortArgsortScatter, THREADS, MINB><<<blocks, THREADS, 0, st>>>(a);
-    else k_sort_scatter<T, FIRST, kSortKeysToValues, THREADS, MINB><<<blocks, THREADS, 0, st>>>(a);
-}
-
 // 256 threads and at most 48 registers (five blocks per SM): measured on the
 // 4096 x 2^16 batch, 5.60 ms of scatter per iteration against 6.18 ms with
 // 64 registers (four blocks) and 9.47 ms with 512-thread blocks.
-template <typename T, bool FIRST>
-static void launch_scatter(int mode, const SortArgs& a, int blocks, cudaStream_t st)
+template <typename T, bool FIRST, bool MULTI>
+static void scatter_v(int mode, const LaunchSet<SortArgs>& s, uint32_t g, cudaStream_t st)
 {
-    launch_scatter_v<T, FIRST, 256, 5>(mode, a, blocks, st);
+    constexpr int TH = 256, MB = 5;
+    if (mode == 0) k_sort_scatter<T, FIRST, 0, TH, MB, MULTI><<<g, TH, 0, st>>>(s);
+    else if (mode == kSortArgsortScatter) k_sort_scatter<T, FIRST, kSortArgsortScatter, TH, MB, MULTI><<<g, TH, 0, st>>>(s);
+    else k_sort_scatter<T, FIRST, kSortKeysToValues, TH, MB, MULTI><<<g, TH, 0, st>>>(s);
+}
+
+template <typename T, bool FIRST>
+static int launch_scatter(int mode, const std::vector<SortArgs>& args, const std::vector<uint32_t>& blocks,
+                          cudaStream_t st)
+{
+    return for_launch_sets(args, blocks, [&](const LaunchSet<SortArgs>& s, uint32_t g, bool multi) {
+        if (multi) scatter_v<T, FIRST, true>(mode, s, g, st);
+        else scatter_v<T, FIRST, false>(mode, s, g, st);
+    });
 }
 
 template <typename T, int TPB>
-static void launch_hist_t(bool first, const SortArgs& a, int ncurves, cudaStream_t st)
+static int launch_hist_t(bool first, const std::vector<SortArgs>& args, const std::vector<uint32_t>& blocks,
+                         cudaStream_t st)
 {
-    const int blocks = ncurves * (a.tpc / TPB);
-    if (first) k_sort_hist<T, true, TPB><<<blocks, kSortThreads, 0, st>>>(a);
-    else k_sort_hist<T, false, TPB><<<blocks, kSortThreads, 0, st>>>(a);
+    return for_launch_sets(args, blocks, [&](const LaunchSet<SortArgs>& s, uint32_t g, bool multi) {
+        if (first && multi) k_sort_hist<T, true, TPB, true><<<g, kSortThreads, 0, st>>>(s);
+        else if (first) k_sort_hist<T, true, TPB, false><<<g, kSortThreads, 0, st>>>(s);
+        else if (multi) k_sort_hist<T, false, TPB, true><<<g, kSortThreads, 0, st>>>(s);
+        else k_sort_hist<T, false, TPB, false><<<g, kSortThreads, 0, st>>>(s);
+    });
+}
+
+// Four tiles per histogram block where a curve has them (measured on the
+// 4096 x 2^16 batch: 1.25 ms of histograms and scans per iteration with one
+// tile per block, 1.02 with two, 1.00 with four): the classes are grouped by
+// tiles per block.
+template <typename T>
+static int launch_hist(bool first, const std::vector<SortArgs>& args, cudaStream_t st)
+{
+    std::vector<SortArgs> g[3];
+    std::vector<uint32_t> b[3];
+    for (const SortArgs& a : args) {
+        const int tpb = std::min(4, a.tpc);
+        const int q = tpb >= 4 ? 2 : (tpb >= 2 ? 1 : 0);
+        g[q].push_back(a);
+        b[q].push_back((uint32_t)(a.ncurves * (a.tpc / (1 << q))));
+    }
+    return launch_hist_t<T, 4>(first, g[2], b[2], st) + launch_hist_t<T, 2>(first, g[1], b[1], st) +
+           launch_hist_t<T, 1>(first, g[0], b[0], st);
+}
+
+// Tile prefixes and digit bases: one launch for the classes whose curves
+// have at most kScanChunk tiles, two (tiles, then chunks) for the others.
+static int launch_scan(const std::vector<SortArgs>& args, cudaStream_t st)
+{
+    std::vector<SortArgs> one, two;
+    std::vector<uint32_t> b_one, b_tiles, b_two;
+    for (const SortArgs& a : args) {
+        if (a.nchunks == 1) {
+            one.push_back(a);
+            b_one.push_back((uint32_t)a.ncurves);
+        } else {
+            two.push_back(a);
+            b_tiles.push_back((uint32_t)(a.ncurves * a.nchunks));
+            b_two.push_back((uint32_t)a.ncurves);
+        }
+    }
+    int n = 0;
+    n += for_launch_sets(one, b_one, [&](const LaunchSet<SortArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_sort_scan_curve<true><<<g, 256, 0, st>>>(s);
+        else k_sort_scan_curve<false><<<g, 256, 0, st>>>(s);
+    });
+    n += for_launch_sets(two, b_tiles, [&](const LaunchSet<SortArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_sort_scan_tiles<true><<<g, 256, 0, st>>>(s);
+        else k_sort_scan_tiles<false><<<g, 256, 0, st>>>(s);
+    });
+    n += for_launch_sets(two, b_two, [&](const LaunchSet<SortArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_sort_scan_chunks<true><<<g, 256, 0, st>>>(s);
+        else k_sort_scan_chunks<false><<<g, 256, 0, st>>>(s);
+    });
+    return n;
 }
 
 template <typename T>
-static void launch_hist(bool first, const SortArgs& a, int ncurves, cudaStream_t st)
+void launch_sort(const Plan& p, const std::vector<const ClassInfo*>& ks, const std::vector<const void*>& srcs,
+                 SortMode mode, bool gated, cudaStream_t st, uint64_t* launches, void* x_out, KernelTimes* kt,
+                 bool presampled)
 {
-    // four tiles per block where a curve has them (measured on the 4096 x 2^16
-    // batch: 1.25 ms of histograms and scans per iteration with one tile per
-    // block, 1.02 with two, 1.00 with four)
-    const int tpb = std::min(4, a.tpc);
-    if (tpb >= 4) launch_hist_t<T, 4>(first, a, ncurves, st);
-    else if (tpb >= 2) launch_hist_t<T, 2>(first, a, ncurves, st);
-    else launch_hist_t<T, 1>(first, a, ncurves, st);
+    std::vector<const ClassInfo*> bk, rk;
+    std::vector<const void*> bsrc, rsrc;
+    for (size_t i = 0; i < ks.size(); ++i) {
+        if (mode == kSortArgsortScatter && ks[i]->bucket) {
+            bk.push_back(ks[i]);
+            bsrc.push_back(srcs[i]);
+        } else {
+            rk.push_back(ks[i]);
+            rsrc.push_back(srcs[i]);
+        }
+    }
+    if (!bk.empty()) launch_bucket_argsort(p, bk, bsrc, x_out, gated, presampled, st, launches, kt);
+    if (rk.empty()) return;
+    using K = typename key_of<T>::type;
+    const int passes = (int)sizeof(K);  // 8-bit digits
+    std::vector<SortArgs> args(rk.size());
+    std::vector<uint32_t> blocks(rk.size());
+    for (size_t i = 0; i < rk.size(); ++i) {
+        const ClassInfo& k = *rk[i];
+        SortArgs& a = args[i];
+        a = SortArgs{};
+        a.cls_curves = k.d_curves;
+        a.curves = p.d_curves;
+        a.eff_iters = p.d_eff_iters;
+        a.d_iter = gated ? p.d_iter : nullptr;
+        a.src = rsrc[i];
+        a.hist = p.d_hist + k.hist_off;
+        a.cbase = p.d_cbase + k.cbase_off;
+        a.x_out = x_out ? x_out : p.d_x;
+        a.s_in = p.d_s;
+        a.s_out = p.d_s;
+        a.ncurves = k.ncurves;
+        a.tpc = k.tiles_per_curve;
+        a.nchunks = k.nchunks;
+        a.tile_len = k.tile_len;
+        blocks[i] = (uint32_t)(k.ncurves * k.tiles_per_curve);
+    }
+    int n = 0;
+    for (int q = 0; q < passes; ++q) {
+        const bool first = q == 0, last = q + 1 == passes;
+        for (SortArgs& a : args) {
+            a.shift = 8 * q;
+            // pass q reads set (q odd ? A : B) ... with pass 0 reading `src`
+            a.keys_in = (q % 2 == 1) ? p.d_keysA : p.d_keysB;
+            a.vals_in = (q % 2 == 1) ? p.d_valsA : p.d_valsB;
+            a.keys_out = (q % 2 == 0) ? p.d_keysA : p.d_keysB;
+            a.vals_out = (q % 2 == 0) ? p.d_valsA : p.d_valsB;
+        }
+        if (kt) kt->begin(kGroupSortHistScan, st);
+        n += launch_hist<T>(first, args, st);
+        n += launch_scan(args, st);
+        if (kt) kt->end(st);
+        const int m = last ? (int)mode : 0;
+        if (kt) kt->begin(kGroupSortScatter, st);
+        if (first) n += launch_scatter<T, true>(m, args, blocks, st);
+        else n += launch_scatter<T, false>(m, args, blocks, st);
+        if (kt) kt->end(st);
+    }
+    if (launches) *launches += (uint64_t)n;
 }
 
 template <typename T>
 void launch_sort(const Plan& p, const ClassInfo& k, const void* src, SortMode mode, bool gated,
                  cudaStream_t st, uint64_t* launches, void* x_out, KernelTimes* kt, bool presampled)
 {
-    if (mode == kSortArgsortScatter && k.bucket) {
-        launch_bucket_argsort(p, k, src, x_out, gated, presampled, st, launches, kt);
-        return;
-    }
-    using K = typename key_of<T>::type;
-    const int passes = (int)sizeof(K);  // 8-bit digits
-    SortArgs a{};
-    a.cls_curves = k.d_curves;
-    a.curves = p.d_curves;
-    a.eff_iters = p.d_eff_iters;
-    a.d_iter = gated ? p.d_iter : nullptr;
-    a.src = src;
-    a.hist = p.d_hist + k.hist_off;
-    a.cbase = p.d_cbase + k.cbase_off;
-    a.x_out = x_out ? x_out : p.d_x;
-    a.s_in = p.d_s;
-    a.s_out = p.d_s;
-    a.ncurves = k.ncurves;
-    a.tpc = k.tiles_per_curve;
-    a.nchunks = k.nchunks;
-    a.tile_len = k.tile_len;
-    const int blocks = k.ncurves * k.tiles_per_curve;
-    for (int q = 0; q < passes; ++q) {
-        const bool first = q == 0, last = q + 1 == passes;
-        a.shift = 8 * q;
-        // pass q reads set (q odd ? A : B) ... with pass 0 reading `src`
-        a.keys_in = (q % 2 == 1) ? p.d_keysA : p.d_keysB;
-        a.vals_in = (q % 2 == 1) ? p.d_valsA : p.d_valsB;
-        a.keys_out = (q % 2 == 0) ? p.d_keysA : p.d_keysB;
-        a.vals_out = (q % 2 == 0) ? p.d_valsA : p.d_valsB;
-        if (kt) kt->begin(kGroupSortHistScan, st);
-        launch_hist<T>(first, a, k.ncurves, st);
-        if (k.nchunks == 1) {
-            k_sort_scan_curve<<<k.ncurves, 256, 0, st>>>(a);
-        } else {
-            k_sort_scan_tiles<<<k.ncurves * k.nchunks, 256, 0, st>>>(a);
-            k_sort_scan_chunks<<<k.ncurves, 256, 0, st>>>(a);
-        }
-        if (kt) kt->end(st);
-        const int m = last ? (int)mode : 0;
-        if (kt) kt->begin(kGroupSortScatter, st);
-        if (first) launch_scatter<T, true>(m, a, blocks, st);
-        else launch_scatter<T, false>(m, a, blocks, st);
-        if (kt) kt->end(st);
-        if (launches) *launches += k.nchunks == 1 ? 3 : 4;
-    }
+    launch_sort<T>(p, std::vector<const ClassInfo*>{&k}, std::vector<const void*>{src}, mode, gated, st, launches,
+                   x_out, kt, presampled);
 }
 
 template void launch_sort<float>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t, uint64_t*,
                                 void*, KernelTimes*, bool);
 template void launch_sort<double>(const Plan&, const ClassInfo&, const void*, SortMode, bool, cudaStream_t,
                                  uint64_t*, void*, KernelTimes*, bool);
+template void launch_sort<float>(const Plan&, const std::vector<const ClassInfo*>&, const std::vector<const void*>&,
+                                 SortMode, bool, cudaStream_t, uint64_t*, void*, KernelTimes*, bool);
+template void launch_sort<double>(const Plan&, const std::vector<const ClassInfo*>&, const std::vector<const void*>&,
+                                  SortMode, bool, cudaStream_t, uint64_t*, void*, KernelTimes*, bool);
 
 }  // namespace lc
