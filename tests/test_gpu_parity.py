@@ -418,10 +418,11 @@ def test_stage_launches_shared_by_classes(monkeypatch):
     (stage, kernel form, radix) -- forward tile pass, fused spectral kernel,
     inverse tile pass, each over the radices 2^6..2^9 that the seven lengths
     use (4 + 4 + 4) --, the sample sort of the 2^13..2^17 classes five
-    launches, the four radix passes of the 2^18 and 2^19 classes three each,
-    and the iteration counter one: 30 per iteration, against 71 with one
-    launch per class and kernel.  Every curve's result is the same, bit for
-    bit, as that curve's run alone."""
+    launches, each of the four radix passes of the 2^18 and 2^19 classes
+    four (histogram, the tile and the chunk scan of curves of more than 32
+    sort tiles, scatter), and the iteration counter one: 34 per iteration,
+    against 79 with one launch per class and kernel.  Every curve's result is
+    the same, bit for bit, as that curve's run alone."""
     from paper_1909_06374_gb300 import lc_plan_last_launches
     monkeypatch.setenv("LC_PATH", "multi")
     jobs = [workloads.job(n, 3, seed=60 + n, curve_id=n, f_br=0.02 if n % 2 else 0.004)
@@ -430,7 +431,7 @@ def test_stage_launches_shared_by_classes(monkeypatch):
         mixed = _np(p.generate())
         p.iterate(1)  # queues the iteration budgets' reset and one iteration
         per_iter = lc_plan_last_launches(p.handle) - 1
-    assert per_iter == 30, per_iter
+    assert per_iter == 34, per_iter
     for c, j in enumerate(jobs):
         with Plan([j], LC_FP32) as q:
             alone = _np(q.generate())
