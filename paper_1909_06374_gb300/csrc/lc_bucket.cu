@@ -3,10 +3,11 @@
 // x_adj) as a sample sort: one bucket pass through HBM and one on-chip pass
 // that ranks every element exactly.
 //
-// Per curve of N = 2^13 .. 2^17 FP32 samples:
-//   k_bk_sample   1024 values of x_adj at a fixed stride (stored by the
-//                 inverse transform's last pass, or gathered here), sorted in
-//                 shared memory; 255 of them become the splitters of 256
+// Per curve of N = 2^13 .. 2^20 FP32 samples:
+//   k_bk_sample   S values of x_adj at a fixed stride (S = 1024 up to 2^17,
+//                 4096 above; stored by the inverse transform's last pass,
+//                 or gathered here), sorted in registers and shared
+//                 memory; every (S/256)-th becomes one of the splitters of 256
 //                 buckets (bucket b holds spl[b-1] <= x < spl[b]); a
 //                 4096-cell grid over the sample's range with, per cell, the
 //                 number of splitters in earlier cells;
@@ -15,8 +16,9 @@
 //                 exceed it; one byte per element kept for the scatter) and
 //                 the tile's bucket counts;
 //   k_bk_scan     tile prefixes and bucket bases of the curve, each bucket's
-//                 bounds, and groups of consecutive buckets of at most kBkCap
-//                 elements, in the curve's own work-item slots;
+//                 bounds, and groups of consecutive buckets of at most CAP
+//                 elements (2048 up to 2^18, N/128 above), in the curve's
+//                 own work-item slots;
 //   k_bk_scatter  per tile: the elements placed in shared memory in bucket
 //                 order (the order inside a bucket is arbitrary), then each
 //                 bucket's run written to the tile's slice of the bucket;
@@ -31,8 +33,8 @@
 //                 (value, position) -- the stable argsort order, whatever
 //                 order the scatter left.  rank = group base + rank in the
 //                 group; the block writes x[position] = s[rank].
-// A bucket of more than kBkCap elements (a spike of equal or nearly equal
-// values) is one group of its own, sorted by a block-level LSD radix sort on
+// A bucket of more than CAP elements (a spike of equal or nearly equal
+// values, or rarely a wide bucket) is one group of its own, sorted by a block-level LSD radix sort on
 // (value, position) through global memory instead.
 //
 // HBM bytes per element: 4 (histogram) + 4 + 1 + 8 (scatter, incl. the
@@ -47,21 +49,32 @@
 namespace lc {
 
 constexpr int kBkBuckets = 256;
-constexpr int kBkSample = 1024;
-constexpr int kBkSampleThreads = 128;
-constexpr int kBkThreads = 512;                  // finish kernel: 4 elements per thread, 4 blocks per SM
-constexpr int kBkPer = kBkCap / kBkThreads;      // elements per finish thread
 constexpr int kBkTileThreads = 256;              // histogram and scatter kernels
+
+// Sample size and finish-group capacity per length.  Up to 2^17: 1024 sample
+// values (four per bucket) and groups of at most 2048 elements.  From 2^18
+// on: 4096 values (16 per bucket: bucket sizes spread less, 0.07% of buckets
+// exceed twice the mean) and groups of twice the mean bucket, N / 128: 2048
+// at 2^18, 4096 at 2^19, 8192 at 2^20.
+int bucket_samples(uint32_t log2n)
+{
+    return log2n >= 18 ? 4096 : 1024;
+}
+
+int bucket_cap(uint32_t log2n)
+{
+    return log2n <= 18 ? kBkCap : (kBkCap << (log2n - 18));
+}
 
 // Auxiliary area of a class (u32 words): a 64-word header (unused), then per
 // curve: splitters (float bits), the curve's min and max (order keys), bucket
 // bases (257), the group count, per-bucket parameters (lower bound, elements
 // per unit value, base, count: 4 words each), the bucket-search grid (lo,
 // cells per unit value) and its table (one byte per cell), the sample of
-// x_adj (kBkSample floats, written by the inverse transform's last pass);
-// then the work items of the finish kernel, gmax slots per curve (e0, n,
-// first bucket, buckets; curve offset lo, hi, class index of the curve, 0: 8
-// words each; n = 0 in the slots after the curve's groups).
+// x_adj (bucket_samples floats, written by the inverse transform's last
+// pass); then the work items of the finish kernel, gmax slots per curve (e0,
+// n, first bucket, buckets; curve offset lo, hi, class index of the curve, 0:
+// 8 words each; n = 0 in the slots after the curve's groups).
 constexpr int kAuxHeader = 64;
 constexpr int kAuxSpl = 0;
 constexpr int kAuxMin = 256;
@@ -72,37 +85,36 @@ constexpr int kAuxPar = 516;                            // 16-byte aligned
 constexpr int kBkCells = 4096;                          // lookup cells of the bucket search
 constexpr int kAuxGrid = kAuxPar + 4 * kBkBuckets;      // lo (float bits), cells per unit value (float bits)
 constexpr int kAuxLut = kAuxGrid + 4;                   // kBkCells bytes: splitters in earlier cells
-constexpr int kAuxSmp = (kAuxLut + kBkCells / 4 + 3) / 4 * 4;  // kBkSample floats
-constexpr int kAuxCurveWords = ((kAuxSmp + kBkSample) + 63) / 64 * 64;
+constexpr int kAuxSmp = (kAuxLut + kBkCells / 4 + 3) / 4 * 4;  // the sample's floats
+
+int bucket_curve_words(uint32_t log2n)
+{
+    return ((kAuxSmp + bucket_samples(log2n)) + 63) / 64 * 64;
+}
 
 float* bucket_sample_area(const ClassInfo& k)
 {
     return (float*)(k.d_aux + kAuxHeader + kAuxSmp);
 }
 
-int bucket_curve_words()
-{
-    return kAuxCurveWords;
-}
-
-// Sample i of a curve of N = 2^log2n samples is x_adj[i N/kBkSample +
-// N/(2 kBkSample)], the real part of complex element d = i 2^shift +
-// 2^(shift-1) with 2^shift = N / (2 kBkSample).
+// Sample i of a curve of N = 2^log2n samples, S = bucket_samples(log2n), is
+// x_adj[i N/S + N/(2 S)], the real part of complex element d = i 2^shift +
+// 2^(shift-1) with 2^shift = N / (2 S).
 uint32_t bucket_sample_shift(uint32_t log2n)
 {
-    return log2n - 11;
+    return log2n - 1 - (bucket_samples(log2n) == 4096 ? 12u : 10u);
 }
-static_assert(kBkSample == 1024, "sample shift");
 
 int bucket_gmax(uint32_t log2n)
 {
-    // greedy groups: any two consecutive ones hold more than kBkCap elements
-    return 2 * (int)(((size_t)1 << log2n) / kBkCap) + 1;
+    // greedy groups: any two consecutive ones hold more than the capacity
+    return 2 * (int)(((size_t)1 << log2n) / (size_t)bucket_cap(log2n)) + 1;
 }
 
 size_t bucket_aux_words(uint32_t log2n, int ncurves)
 {
-    return (size_t)kAuxHeader + (size_t)ncurves * kAuxCurveWords + 8 * (size_t)ncurves * bucket_gmax(log2n);
+    return (size_t)kAuxHeader + (size_t)ncurves * bucket_curve_words(log2n) +
+           8 * (size_t)ncurves * bucket_gmax(log2n);
 }
 
 bool bucket_supported(lc_precision prec, uint32_t log2n)
@@ -123,7 +135,7 @@ struct BkArgs {
     const int* d_iter;       // null: every curve active
     const float* xadj;       // values to rank (the inverse transform's output)
     int presampled;          // the sample is in the aux area already
-    uint32_t* aux;           // [ci][kAuxCurveWords]
+    uint32_t* aux;           // [ci][cw]
     uint4* items;            // [2 * (ci gmax + g)]: e0, n, first bucket, buckets; off lo, hi, ci, 0
     uint32_t* hist;          // [ci][tpc][256]
     uint32_t* bid;           // bucket of every element, one byte each (four per word)
@@ -135,6 +147,8 @@ struct BkArgs {
     float* x_out;            // x[position] = s[rank]
     int tpc;
     int gmax;
+    int cw;                  // aux words per curve
+    int cap;                 // finish-group capacity (elements)
     uint32_t log2n;
 };
 
@@ -194,25 +208,26 @@ __device__ __forceinline__ int cell_slot(int c)
     return c + (c >> 5);
 }
 
-// One block of 128 threads per curve.  The 1024 sample values are sorted by a
-// bitonic network held in registers: thread (warp w, lane l) keeps element
-// 32 (8 w + i) + l in v[i], i < 8, so the stages with a partner distance j < 32
-// exchange through warp shuffles, those with j = 32, 64, 128 stay inside the
-// thread, and only j = 256 and 512 go through shared memory.
-template <bool MULTI>
-__global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const __grid_constant__ LaunchSet<BkArgs> set)
+// One block of S / 8 threads per curve (S = 1024 or 4096 sample values).  The
+// sample is sorted by a bitonic network held in registers: thread (warp w,
+// lane l) keeps element 32 (8 w + i) + l in v[i], i < 8, so the stages with a
+// partner distance j < 32 exchange through warp shuffles, those with j = 32,
+// 64, 128 stay inside the thread, and only j >= 256 go through shared memory.
+template <int S, bool MULTI>
+__global__ void __launch_bounds__(S / 8) k_bk_sample(const __grid_constant__ LaunchSet<BkArgs> set)
 {
     uint32_t blk;
     const BkArgs& a = set.pick<MULTI>(blk);
-    static_assert(kBkSample == 1024 && kBkSampleThreads == 128, "register layout of the sample sort");
-    constexpr int PER = kBkSample / kBkSampleThreads;  // 8 elements per thread
+    constexpr int TH = S / 8;  // 8 elements per thread
+    constexpr int PER = 8;
+    static_assert(S == 1024 || S == 4096, "register layout of the sample sort");
     const int ci = (int)blk;
     const int c = a.cls_curves[ci];
     if (!bk_active(a, c)) return;
-    __shared__ float sm[kBkSample];
+    __shared__ float sm[S];
     __shared__ uint32_t cnt[kBkCells + kBkCells / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t* A0 = a.aux + (size_t)ci * kAuxCurveWords;
+    const uint32_t* A0 = a.aux + (size_t)ci * a.cw;
     float v[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
@@ -220,13 +235,13 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const __grid_con
         if (a.presampled) {
             v[i] = __uint_as_float(A0[kAuxSmp + e]);
         } else {
-            const uint32_t stride = (1u << a.log2n) / kBkSample;
+            const uint32_t stride = (1u << a.log2n) / (uint32_t)S;
             v[i] = a.xadj[a.curves[c].off + (uint64_t)e * stride + stride / 2];
         }
     }
-    for (int i = tid; i < kBkCells + kBkCells / 32; i += kBkSampleThreads) cnt[i] = 0u;
+    for (int i = tid; i < kBkCells + kBkCells / 32; i += TH) cnt[i] = 0u;
     // bitonic sort, ascending
-    for (int k = 2; k <= kBkSample; k <<= 1) {
+    for (int k = 2; k <= S; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j < 32) {
                 const bool lower = (lane & j) == 0;
@@ -256,14 +271,14 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const __grid_con
 #pragma unroll
     for (int i = 0; i < PER; ++i) sm[32 * (8 * warp + i) + lane] = v[i];
     __syncthreads();
-    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
+    uint32_t* A = a.aux + (size_t)ci * a.cw;
     // splitters; the search grid spans the sample's range
-    const float glo = sm[0], ghi = sm[kBkSample - 1];
+    const float glo = sm[0], ghi = sm[S - 1];
     const float d = ghi - glo;
     const float gscale = d > 0.0f ? (float)kBkCells / d : 0.0f;
-    for (int i = tid; i < kBkBuckets; i += kBkSampleThreads) {
+    for (int i = tid; i < kBkBuckets; i += TH) {
         if (i < kBkBuckets - 1) {
-            const float sv = sm[(kBkSample / kBkBuckets) * (i + 1)];
+            const float sv = sm[(S / kBkBuckets) * (i + 1)];
             A[kAuxSpl + i] = __float_as_uint(sv);
             atomicAdd(&cnt[cell_slot(grid_cell(sv, glo, gscale))], 1u);
         } else {
@@ -282,8 +297,8 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const __grid_con
     // lut[c] = splitters in cells below c: exclusive scan of the cell counts
     // (thread tid owns kBkCells / threads consecutive cells)
     {
-        constexpr int CPT = kBkCells / kBkSampleThreads;  // 32
-        static_assert(CPT == 32, "one padded row of cells per thread");
+        constexpr int CPT = kBkCells / TH;  // 32 or 8
+        static_assert(CPT % 4 == 0, "whole table words per thread");
         const int c0 = tid * CPT;
         uint32_t run = 0;
 #pragma unroll
@@ -294,7 +309,7 @@ __global__ void __launch_bounds__(kBkSampleThreads) k_bk_sample(const __grid_con
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        __shared__ uint32_t wsum[kBkSampleThreads / 32];
+        __shared__ uint32_t wsum[TH / 32];
         if (lane == 31) wsum[warp] = incl;
         __syncthreads();
         uint32_t acc = incl - run;
@@ -331,7 +346,7 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const __grid_constan
     __shared__ uint32_t lutw[kBkCells / 4];
     __shared__ uint32_t h[TPB][kBkBuckets];
     const int tid = threadIdx.x;
-    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
+    uint32_t* A = a.aux + (size_t)ci * a.cw;
     spl[tid] = __uint_as_float(A[kAuxSpl + tid]);
     for (int i = tid; i < kBkCells / 4; i += kBkTileThreads) lutw[i] = A[kAuxLut + i];
     const float glo = __uint_as_float(A[kAuxGrid]), gscale = __uint_as_float(A[kAuxGrid + 1]);
@@ -371,10 +386,10 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_hist(const __grid_constan
 // take its gmax work-item slots in order; the slots after them are marked
 // empty (n = 0), and so are all of them for a curve that has stopped.
 // Groups: the group that starts at bucket s ends before bucket e = the last
-// index with base[e] - base[s] <= kBkCap (at least s + 1: a larger bucket is a
+// index with base[e] - base[s] <= cap (at least s + 1: a larger bucket is a
 // group of its own), found for every s at once by binary search; thread 0
 // then follows these links from bucket 0.  Any two consecutive groups hold
-// more than kBkCap elements, so a curve has at most gmax = 2 N / kBkCap + 1.
+// more than cap elements, so a curve has at most gmax = 2 N / cap + 1.
 template <bool MULTI>
 __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const __grid_constant__ LaunchSet<BkArgs> set)
 {
@@ -394,7 +409,7 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const __grid_constant__ 
     __shared__ uint32_t gs[kBkBuckets + 1];
     __shared__ uint32_t ng;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
+    uint32_t* A = a.aux + (size_t)ci * a.cw;
     // the bucket's bounds (read before the counts, so both loads overlap)
     const float lo = tid == 0 ? key_value(A[kAuxMin]) : __uint_as_float(A[kAuxSpl + tid - 1]);
     const float hi = tid == kBkBuckets - 1 ? key_value(A[kAuxMax]) : __uint_as_float(A[kAuxSpl + tid]);
@@ -443,7 +458,7 @@ __global__ void __launch_bounds__(kBkBuckets) k_bk_scan(const __grid_constant__ 
     }
     __syncthreads();
     {
-        const uint32_t target = base + (uint32_t)kBkCap;
+        const uint32_t target = base + (uint32_t)a.cap;
         int l = tid + 1, r = kBkBuckets;  // last e in [tid + 1, 256] with bs[e] <= target, else tid + 1
         while (l < r) {
             const int mid = (l + r + 1) >> 1;
@@ -497,7 +512,7 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_scatter(const __grid_cons
     __shared__ uint32_t gb[kBkBuckets];
     __shared__ uint32_t wsum[kBkTileThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t* A = a.aux + (size_t)ci * kAuxCurveWords;
+    const uint32_t* A = a.aux + (size_t)ci * a.cw;
     const uint64_t off = a.curves[c].off;
     const uint32_t e0 = (uint32_t)t * kSortTile;
     const float4* __restrict__ src = (const float4*)(a.xadj + off + e0);
@@ -556,7 +571,8 @@ __global__ void __launch_bounds__(kBkTileThreads) k_bk_scatter(const __grid_cons
 }
 
 // ------------------------------------------------------------------ finish
-// Block-wide exclusive scan of v (kBkThreads threads).
+// Block-wide exclusive scan of v (TH threads).
+template <int TH>
 __device__ __forceinline__ uint32_t bk_block_scan(uint32_t v, uint32_t* wsum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -570,7 +586,7 @@ __device__ __forceinline__ uint32_t bk_block_scan(uint32_t v, uint32_t* wsum)
     __syncthreads();
     uint32_t woff = 0;
 #pragma unroll
-    for (int w = 0; w < kBkThreads / 32; ++w) woff += w < warp ? wsum[w] : 0u;
+    for (int w = 0; w < TH / 32; ++w) woff += w < warp ? wsum[w] : 0u;
     __syncthreads();
     return woff + incl - v;
 }
@@ -579,26 +595,26 @@ __device__ __forceinline__ uint32_t bk_block_scan(uint32_t v, uint32_t* wsum)
 // by the byte `shift` of the position (val, bits 0..23) when !KEYB, else of
 // the value's order key.  Returns false (nothing moved) when every element
 // has the same digit.
-template <bool KEYB>
+template <bool KEYB, int TH>
 __device__ bool bk_block_pass(const uint32_t* __restrict__ ik, const uint32_t* __restrict__ iv,
                               uint32_t* __restrict__ ok, uint32_t* __restrict__ ov, int n, int shift,
                               uint32_t* hist, uint32_t (*wc)[256], uint32_t* wsum)
 {
-    constexpr int W = kBkThreads / 32;
+    constexpr int W = TH / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto digit = [&](uint32_t k, uint32_t v) -> uint32_t {
         return KEYB ? (order_key(__uint_as_float(k)) >> shift) & 255u : ((v & 0xffffffu) >> shift) & 255u;
     };
-    static_assert(kBkThreads >= 256, "one thread per digit");
+    static_assert(TH >= 256, "one thread per digit");
     if (tid < 256) hist[tid] = 0;
     __syncthreads();
-    for (int i = tid; i < n; i += kBkThreads) atomicAdd(&hist[digit(ik[i], iv[i])], 1u);
+    for (int i = tid; i < n; i += TH) atomicAdd(&hist[digit(ik[i], iv[i])], 1u);
     __syncthreads();
     if (__syncthreads_or(tid < 256 && hist[tid] == (uint32_t)n)) return false;
-    uint32_t base = bk_block_scan(tid < 256 ? hist[tid] : 0u, wsum);  // digit tid's first output index
+    uint32_t base = bk_block_scan<TH>(tid < 256 ? hist[tid] : 0u, wsum);  // digit tid's first output index
     const uint32_t lt = (1u << lane) - 1u;
-    for (int c0 = 0; c0 < n; c0 += kBkThreads) {
-        for (int q = tid; q < W * 256; q += kBkThreads) (&wc[0][0])[q] = 0;
+    for (int c0 = 0; c0 < n; c0 += TH) {
+        for (int q = tid; q < W * 256; q += TH) (&wc[0][0])[q] = 0;
         __syncthreads();
         const int i = c0 + tid;
         const bool valid = i < n;
@@ -635,11 +651,12 @@ __device__ bool bk_block_pass(const uint32_t* __restrict__ ik, const uint32_t* _
 
 // Oversize bucket: sort its n pairs by (order key, position) with block LSD
 // passes (position bytes first), then x[position] = s[e0 + r].
+template <int TH>
 __device__ void bk_oversize(const BkArgs& a, uint64_t off, uint32_t e0, int n, uint32_t* smem_u32)
 {
     uint32_t* hist = smem_u32;
     uint32_t(*wc)[256] = (uint32_t(*)[256])(smem_u32 + 256);
-    uint32_t* wsum = smem_u32 + 256 + (kBkThreads / 32) * 256;
+    uint32_t* wsum = smem_u32 + 256 + (TH / 32) * 256;
     uint32_t* k0 = a.keys + off + e0;
     uint32_t* v0 = a.vals + off + e0;
     uint32_t* k1 = a.keys2 + off + e0;
@@ -653,14 +670,14 @@ __device__ void bk_oversize(const BkArgs& a, uint64_t off, uint32_t e0, int n, u
         const uint32_t* iv = in0 ? v0 : v1;
         uint32_t* ok = in0 ? k1 : k0;
         uint32_t* ov = in0 ? v1 : v0;
-        const bool moved = keyb ? bk_block_pass<true>(ik, iv, ok, ov, n, shift, hist, wc, wsum)
-                                : bk_block_pass<false>(ik, iv, ok, ov, n, shift, hist, wc, wsum);
+        const bool moved = keyb ? bk_block_pass<true, TH>(ik, iv, ok, ov, n, shift, hist, wc, wsum)
+                                : bk_block_pass<false, TH>(ik, iv, ok, ov, n, shift, hist, wc, wsum);
         if (moved) in0 = !in0;
     }
     const uint32_t* vf = in0 ? v0 : v1;
     const float* __restrict__ s = a.s + off + e0;
     float* __restrict__ x = a.x_out + off;
-    for (int r = threadIdx.x; r < n; r += kBkThreads) x[vf[r] & 0xffffffu] = s[r];
+    for (int r = threadIdx.x; r < n; r += TH) x[vf[r] & 0xffffffu] = s[r];
 }
 
 // Sub-buckets per element of a bucket (linear interpolation of the value
@@ -669,25 +686,39 @@ __device__ void bk_oversize(const BkArgs& a, uint64_t off, uint32_t e0, int n, u
 // per element cost no more shared memory or scan steps than one 32-bit
 // counter per element.
 constexpr int kBkSubPer = 2;
-constexpr int kBkNsub = kBkSubPer * kBkCap;
 
-// Shared memory of the finish kernel (u32 words): the 64-bit keys (order key
-// of the value << 32 | position) of the elements that share a sub-bucket, at
-// their sub-bucket's start + arrival index; sub-bucket counts, then starts
-// (nsub + 1, 16 bits each, two to a word); per-bucket parameters; scan
-// partials.
-constexpr int kFinKk = 0;                           // kBkCap u64
-constexpr int kFinSt = 2 * kBkCap;                  // kBkNsub / 2 + 1 words (+3 pad)
-constexpr int kFinPar = kFinSt + kBkNsub / 2 + 4;   // float2 lo/scale, uint2 first/count: 4 x 256
-constexpr int kFinWs = kFinPar + 4 * kBkBuckets;    // 8
-constexpr int kFinWords = kFinWs + 32;
-static_assert(kFinWords >= 256 + (kBkThreads / 32) * 256 + 16, "oversize sort scratch");
+// Finish kernel of groups of at most CAP elements: 512 threads of four
+// elements (four blocks per SM) at CAP = 2048, 1024 threads of four (two
+// blocks per SM) at 4096, 1024 threads of eight (one block per SM) at 8192.
+// Shared memory (u32 words): the 64-bit keys (order key of the value << 32 |
+// position) of the elements that share a sub-bucket, at their sub-bucket's
+// start + arrival index; sub-bucket counts, then starts (nsub + 1, 16 bits
+// each, two to a word); per-bucket parameters; scan partials.
+template <int CAP>
+struct FinLayout {
+    static constexpr int THREADS = CAP == 2048 ? 512 : 1024;
+    static constexpr int PER = CAP / THREADS;            // elements per thread
+    static constexpr int MINB = CAP == 2048 ? 4 : (CAP == 4096 ? 2 : 1);
+    static constexpr int NSUB = kBkSubPer * CAP;
+    static constexpr int KK = 0;                         // CAP u64
+    static constexpr int ST = 2 * CAP;                   // NSUB / 2 + 1 words (+3 pad)
+    static constexpr int PAR = ST + NSUB / 2 + 4;        // float2 lo/scale, uint2 first/count: 4 x 256
+    static constexpr int WS = PAR + 4 * kBkBuckets;      // THREADS / 32
+    static constexpr int WORDS = WS + 32;
+    static constexpr size_t SMEM = (size_t)WORDS * 4;
+    static_assert(WORDS >= 256 + (THREADS / 32) * 256 + 16, "oversize sort scratch");
+    static_assert(THREADS / 32 <= 32, "scan partials");
+    static_assert(NSUB <= 65536 && CAP <= 65535, "sub-bucket, arrival index and starts in 16 bits");
+};
 
 // One work-item slot per block (gmax slots per curve); a block whose slot is
 // empty returns at once.
-template <bool MULTI>
-__global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_constant__ LaunchSet<BkArgs> set)
+template <int CAP, bool MULTI>
+__global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
+    k_bk_finish(const __grid_constant__ LaunchSet<BkArgs> set)
 {
+    using L = FinLayout<CAP>;
+    constexpr int TH = L::THREADS, PER = L::PER;
     uint32_t blk;
     const BkArgs& a = set.pick<MULTI>(blk);
     constexpr uint32_t kPosMask = (1u << 24) - 1u;
@@ -698,32 +729,32 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_consta
     const int n = (int)d0.y, nb = (int)d0.w;
     if (n == 0) return;
     const uint64_t off = (uint64_t)d1.x | ((uint64_t)d1.y << 32);
-    const uint32_t* A = a.aux + (size_t)d1.z * kAuxCurveWords;
+    const uint32_t* A = a.aux + (size_t)d1.z * a.cw;
     extern __shared__ __align__(16) uint32_t bsm[];
-    if (n > kBkCap) {  // one bucket of nearly equal values
-        bk_oversize(a, off, e0, n, bsm);
+    if (n > CAP) {  // one bucket of nearly equal values
+        bk_oversize<TH>(a, off, e0, n, bsm);
         return;
     }
     const int ns = kBkSubPer * n;  // sub-buckets of the group
-    unsigned long long* kk = (unsigned long long*)(bsm + kFinKk);
-    uint32_t* st = bsm + kFinSt;
-    float2* plo = (float2*)(bsm + kFinPar);                 // (lower bound, sub-buckets per unit)
-    uint2* pof = (uint2*)(bsm + kFinPar + 2 * kBkBuckets);  // (first sub-bucket, sub-buckets)
-    uint32_t* wsum = bsm + kFinWs;
+    unsigned long long* kk = (unsigned long long*)(bsm + L::KK);
+    uint32_t* st = bsm + L::ST;
+    float2* plo = (float2*)(bsm + L::PAR);                 // (lower bound, sub-buckets per unit)
+    uint2* pof = (uint2*)(bsm + L::PAR + 2 * kBkBuckets);  // (first sub-bucket, sub-buckets)
+    uint32_t* wsum = bsm + L::WS;
     const int tid = threadIdx.x;
     const uint32_t* __restrict__ kin = a.keys + off + e0;
     const uint32_t* __restrict__ vin = a.vals + off + e0;
-    float key[kBkPer];
-    uint32_t pos[kBkPer], sub[kBkPer];
+    float key[PER];
+    uint32_t pos[PER], sub[PER];
 #pragma unroll
-    for (int j = 0; j < kBkPer; ++j) {
-        const int p = tid + j * kBkThreads;
+    for (int j = 0; j < PER; ++j) {
+        const int p = tid + j * TH;
         if (p < n) {
             key[j] = __uint_as_float(kin[p]);
             pos[j] = vin[p];
         }
     }
-    static_assert(kBkThreads >= kBkBuckets, "one thread per bucket of a group");
+    static_assert(TH >= kBkBuckets, "one thread per bucket of a group");
     if (tid < nb) {
         const uint4 P = ((const uint4*)(A + kAuxPar))[b0 + (uint32_t)tid];
         // P.y: elements per unit value; kBkSubPer sub-buckets per element
@@ -731,14 +762,14 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_consta
         pof[tid] = make_uint2((uint32_t)kBkSubPer * (P.z - e0), (uint32_t)kBkSubPer * P.w);
     }
     const int nw = ns / 2;  // words of the 16-bit counters
-    for (int i = tid; i <= nw; i += kBkThreads) st[i] = 0u;
+    for (int i = tid; i <= nw; i += TH) st[i] = 0u;
     __syncthreads();
     // count: the sub-bucket of every element (kBkSubPer per element of its
     // bucket, by linear interpolation between the bucket's bounds: monotone in
     // the value) and its arrival index in it
 #pragma unroll
-    for (int j = 0; j < kBkPer; ++j) {
-        const int p = tid + j * kBkThreads;
+    for (int j = 0; j < PER; ++j) {
+        const int p = tid + j * TH;
         if (p < n) {
             const uint32_t bl = min((pos[j] >> 24) - b0, (uint32_t)nb - 1u);
             pos[j] &= kPosMask;
@@ -757,9 +788,8 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_consta
     // owns the consecutive words from kSc tid); st16[ns] = n
     uint16_t* st16 = (uint16_t*)st;
     {
-        constexpr int kSc = kBkNsub / 2 / kBkThreads;
+        constexpr int kSc = L::NSUB / 2 / TH;
         static_assert(kSc % 4 == 0, "16-byte loads");
-        static_assert(kBkNsub <= 65536 && kBkCap <= 65535, "sub-bucket, arrival index and starts in 16 bits");
         const int q0 = tid * kSc;
         // the counts are read twice (sum, then prefixes) to keep them out of
         // registers while the elements' state is live
@@ -774,7 +804,7 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_consta
                     if (q0 + j + t < nw) sum += (w[t] & 0xffffu) + (w[t] >> 16);
             }
         }
-        uint32_t run = bk_block_scan(sum, wsum);
+        uint32_t run = bk_block_scan<TH>(sum, wsum);
 #pragma unroll
         for (int j = 0; j < kSc; j += 4) {
             if (q0 + j < nw) {
@@ -798,10 +828,10 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_consta
     // an element alone in its sub-bucket has rank = the sub-bucket's start;
     // the members of a shared sub-bucket are placed at start + arrival index
     // and ranked below.  rk[j] = the start; sub[j] = members | arrival << 16
-    uint32_t rk[kBkPer];
+    uint32_t rk[PER];
 #pragma unroll
-    for (int j = 0; j < kBkPer; ++j) {
-        const int p = tid + j * kBkThreads;
+    for (int j = 0; j < PER; ++j) {
+        const int p = tid + j * TH;
         if (p < n) {
             const uint32_t u = sub[j] & 0xffffu, old = sub[j] >> 16;
             const uint32_t s0 = st16[u];
@@ -815,8 +845,8 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_consta
     const float* __restrict__ s = a.s + off + e0;
     float* __restrict__ x = a.x_out + off;
 #pragma unroll
-    for (int j = 0; j < kBkPer; ++j) {
-        const int p = tid + j * kBkThreads;
+    for (int j = 0; j < PER; ++j) {
+        const int p = tid + j * TH;
         if (p < n) {
             uint32_t r = rk[j];
             const uint32_t c = sub[j] & 0xffffu;
@@ -833,15 +863,42 @@ __global__ void __launch_bounds__(kBkThreads, 4) k_bk_finish(const __grid_consta
     }
 }
 
-constexpr size_t kBkFinishSmem = (size_t)kFinWords * 4;
+
+template <int CAP>
+static cudaError_t finish_attrs()
+{
+    const int smem = (int)FinLayout<CAP>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_bk_finish<CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bk_finish<CAP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
 
 cudaError_t bucket_kernel_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_bk_finish<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kBkFinishSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_bk_finish<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBkFinishSmem);
+    cudaError_t e = finish_attrs<2048>();
+    if (e == cudaSuccess) e = finish_attrs<4096>();
+    if (e == cudaSuccess) e = finish_attrs<8192>();
     return e;
+}
+
+template <int S>
+static int launch_sample_sets(const std::vector<BkArgs>& args, const std::vector<uint32_t>& blocks, cudaStream_t st)
+{
+    return for_launch_sets(args, blocks, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_sample<S, true><<<g, S / 8, 0, st>>>(s);
+        else k_bk_sample<S, false><<<g, S / 8, 0, st>>>(s);
+    });
+}
+
+template <int CAP>
+static int launch_finish_sets(const std::vector<BkArgs>& args, const std::vector<uint32_t>& blocks, cudaStream_t st)
+{
+    using L = FinLayout<CAP>;
+    return for_launch_sets(args, blocks, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_finish<CAP, true><<<g, L::THREADS, L::SMEM, st>>>(s);
+        else k_bk_finish<CAP, false><<<g, L::THREADS, L::SMEM, st>>>(s);
+    });
 }
 
 template <int TPB>
@@ -876,7 +933,7 @@ void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& k
         a.d_iter = gated ? p.d_iter : nullptr;
         a.xadj = (const float*)srcs[i];
         a.aux = k.d_aux + kAuxHeader;
-        a.items = (uint4*)(k.d_aux + kAuxHeader + (size_t)k.ncurves * kAuxCurveWords);
+        a.items = (uint4*)(k.d_aux + kAuxHeader + (size_t)k.ncurves * bucket_curve_words(k.log2n));
         a.hist = p.d_hist + k.hist_off;
         a.bid = p.d_valsB;  // free until the finish: the bucket bytes of curve c at word off_c
         a.keys = (uint32_t*)p.d_keysA;
@@ -887,6 +944,8 @@ void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& k
         a.x_out = (float*)(x_out ? x_out : p.d_x);
         a.tpc = k.tiles_per_curve;
         a.gmax = bucket_gmax(k.log2n);
+        a.cw = bucket_curve_words(k.log2n);
+        a.cap = bucket_cap(k.log2n);
         a.log2n = k.log2n;
         b_curve[i] = (uint32_t)k.ncurves;
         b_tile[i] = (uint32_t)(k.ncurves * a.tpc);
@@ -901,10 +960,17 @@ void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& k
     }
     int n = 0;
     if (kt) kt->begin(kGroupSortHistScan, st);
-    n += for_launch_sets(args, b_curve, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
-        if (multi) k_bk_sample<true><<<g, kBkSampleThreads, 0, st>>>(s);
-        else k_bk_sample<false><<<g, kBkSampleThreads, 0, st>>>(s);
-    });
+    {
+        // one launch per sample size
+        std::vector<BkArgs> s1, s4;
+        std::vector<uint32_t> b1, b4;
+        for (size_t i = 0; i < nk; ++i) {
+            (bucket_samples(args[i].log2n) == 4096 ? s4 : s1).push_back(args[i]);
+            (bucket_samples(args[i].log2n) == 4096 ? b4 : b1).push_back(b_curve[i]);
+        }
+        n += launch_sample_sets<1024>(s1, b1, st);
+        n += launch_sample_sets<4096>(s4, b4, st);
+    }
     n += launch_hist_sets<2>(h2, hb2, st);
     n += launch_hist_sets<1>(h1, hb1, st);
     n += for_launch_sets(args, b_curve, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
@@ -917,10 +983,19 @@ void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& k
         if (multi) k_bk_scatter<true><<<g, kBkTileThreads, 0, st>>>(s);
         else k_bk_scatter<false><<<g, kBkTileThreads, 0, st>>>(s);
     });
-    n += for_launch_sets(args, b_item, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
-        if (multi) k_bk_finish<true><<<g, kBkThreads, kBkFinishSmem, st>>>(s);
-        else k_bk_finish<false><<<g, kBkThreads, kBkFinishSmem, st>>>(s);
-    });
+    {
+        // one launch per finish capacity
+        std::vector<BkArgs> f[3];
+        std::vector<uint32_t> fb[3];
+        for (size_t i = 0; i < nk; ++i) {
+            const int q = args[i].cap == 2048 ? 0 : (args[i].cap == 4096 ? 1 : 2);
+            f[q].push_back(args[i]);
+            fb[q].push_back(b_item[i]);
+        }
+        n += launch_finish_sets<2048>(f[0], fb[0], st);
+        n += launch_finish_sets<4096>(f[1], fb[1], st);
+        n += launch_finish_sets<8192>(f[2], fb[2], st);
+    }
     if (kt) kt->end(st);
     if (launches) *launches += (uint64_t)n;
 }

@@ -985,7 +985,7 @@ void launch_fft_iteration(const Plan& p, const std::vector<const ClassInfo*>& ks
             x.a.in = x.cur; x.a.out = x.nxt; x.a.log2p = x.log2p;
             if (r == 0 && x.k->bucket && sizeof(T) == 4) {  // the sample sort's sample of x_adj
                 x.a.smp = bucket_sample_area(*x.k);
-                x.a.smp_words = (uint32_t)bucket_curve_words();
+                x.a.smp_words = (uint32_t)bucket_curve_words(x.k->log2n);
                 x.a.smp_shift = bucket_sample_shift(x.k->log2n);
             }
             sel.emplace_back((int)i, x.lr[r]);

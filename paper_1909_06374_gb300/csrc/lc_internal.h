@@ -250,10 +250,13 @@ template <typename T> void launch_sort(const Plan& p, const std::vector<const Cl
                                        bool presampled);
 // sample-sort argsort of the iteration (lc_bucket.cu): FP32 curves of
 // 2^kBkMinLog2 .. 2^kBkMaxLog2 samples (256 buckets of N/256 elements on
-// average); groups of at most kBkCap elements are ranked in shared memory
+// average); groups of at most bucket_cap(log2n) elements (kBkCap up to 2^18,
+// N/128 above) are ranked in shared memory
 constexpr int kBkCap = 2048;
 constexpr uint32_t kBkMinLog2 = 13;
-constexpr uint32_t kBkMaxLog2 = 17;
+constexpr uint32_t kBkMaxLog2 = 20;
+int bucket_samples(uint32_t log2n);  // values in the splitter sample
+int bucket_cap(uint32_t log2n);      // elements of a finish group at most
 bool bucket_supported(lc_precision prec, uint32_t log2n);
 // LC_SORT=radix keeps the LSD radix argsort for every length
 bool bucket_enabled_from_env();
@@ -269,10 +272,10 @@ void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& k
                            const std::vector<const void*>& srcs, void* x_out, bool gated, bool presampled,
                            cudaStream_t st, uint64_t* launches, KernelTimes* kt);
 // where the inverse transform's last pass writes the class's samples of
-// x_adj (curve ci at + ci bucket_curve_words() floats), and the shift of
+// x_adj (curve ci at + ci bucket_curve_words(log2n) floats), and the shift of
 // their complex index (PassArgs::smp_shift)
 float* bucket_sample_area(const ClassInfo& k);
-int bucket_curve_words();
+int bucket_curve_words(uint32_t log2n);
 uint32_t bucket_sample_shift(uint32_t log2n);
 // Eq. 4 partial sums of a multi-kernel class between the state x_{i-1} and
 // the new iterate x_i in `xnew` (one double per sort tile, curve-major, in

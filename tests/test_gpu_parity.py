@@ -413,25 +413,27 @@ def test_classes_sharing_tile_kernels_one_step():
 
 
 def test_stage_launches_shared_by_classes(monkeypatch):
-    """Curves of 2^13 .. 2^19 samples on the multi-kernel path share the
-    launches of each iteration stage: the transforms take one launch per
-    (stage, kernel form, radix) -- forward tile pass, fused spectral kernel,
-    inverse tile pass, each over the radices 2^6..2^9 that the seven lengths
-    use (4 + 4 + 4) --, the sample sort of the 2^13..2^17 classes five
-    launches, each of the four radix passes of the 2^18 and 2^19 classes
-    four (histogram, the tile and the chunk scan of curves of more than 32
-    sort tiles, scatter), and the iteration counter one: 34 per iteration,
-    against 79 with one launch per class and kernel.  Every curve's result is
-    the same, bit for bit, as that curve's run alone."""
+    """Curves of 2^13 .. 2^19, 2^21 and 2^22 samples on the multi-kernel path
+    share the launches of each iteration stage.  Transforms: one launch per
+    (stage, kernel form, radix) -- the first forward tile pass over the radices
+    2^6..2^9, the second one of the 2^21 and 2^22 curves (radix 2^7), the
+    fused spectral kernels over 2^6..2^9, and the inverse passes alike: 4 + 1 +
+    4 + 1 + 4 = 14.  Sample sort of 2^13..2^19: the sample kernel per sample
+    size (1024 values up to 2^17, 4096 above), histogram, scan and scatter
+    once, the finish per group capacity (2048 up to 2^18, 4096 at 2^19): 7.
+    Radix argsort of 2^21 and 2^22: four passes of histogram, tile scan, chunk
+    scan and scatter: 16.  With the iteration counter, 38 launches per
+    iteration, against 99 with one launch per class and kernel.  Every curve's
+    result is the same, bit for bit, as that curve's run alone."""
     from paper_1909_06374_gb300 import lc_plan_last_launches
     monkeypatch.setenv("LC_PATH", "multi")
-    jobs = [workloads.job(n, 3, seed=60 + n, curve_id=n, f_br=0.02 if n % 2 else 0.004)
-            for n in range(13, 20)]
+    lengths = list(range(13, 20)) + [21, 22]
+    jobs = [workloads.job(n, 3, seed=60 + n, curve_id=n, f_br=0.02 if n % 2 else 0.004) for n in lengths]
     with Plan(jobs, LC_FP32) as p:
         mixed = _np(p.generate())
         p.iterate(1)  # queues the iteration budgets' reset and one iteration
         per_iter = lc_plan_last_launches(p.handle) - 1
-    assert per_iter == 34, per_iter
+    assert per_iter == 38, per_iter
     for c, j in enumerate(jobs):
         with Plan([j], LC_FP32) as q:
             alone = _np(q.generate())

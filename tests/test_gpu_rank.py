@@ -3,9 +3,10 @@ own, through the C ABI: out[perm[r]] = s[r] with perm the stable argsort of the
 given values, against the oracle's argsort, bit for bit (integer index work).
 
 The values are chosen to hit every branch of both sort paths: the sample sort
-of FP32 curves of 2^13..2^17 samples (splitters from a sample, buckets, groups
-ranked in shared memory, oversize buckets sorted by block radix passes) and
-the LSD radix passes of the other lengths and of FP64."""
+of FP32 curves of 2^13..2^20 samples (splitters from a sample of 1024 or 4096
+values, buckets, groups of up to 2048, 4096 or 8192 elements ranked in shared
+memory, oversize buckets sorted by block radix passes) and the LSD radix
+passes of the other lengths and of FP64."""
 import numpy as np
 import pytest
 
@@ -62,8 +63,12 @@ def test_rank_replace_fp32_sample_sort_lengths():
     _check(LC_FP32, [13, 14, 15, 16, 17], seed=1)
 
 
+def test_rank_replace_fp32_long_sample_sort_lengths():
+    _check(LC_FP32, [18, 19, 20], seed=5)
+
+
 def test_rank_replace_fp32_radix_lengths():
-    _check(LC_FP32, [4, 9, 12, 18, 19], seed=2)
+    _check(LC_FP32, [4, 9, 12, 21], seed=2)
 
 
 def test_rank_replace_fp64():
@@ -73,8 +78,10 @@ def test_rank_replace_fp64():
 def test_rank_replace_radix_override_agrees(monkeypatch):
     """LC_SORT=radix keeps the LSD passes at every length: the same output."""
     rng = np.random.default_rng(4)
-    jobs = [workloads.job(16, 1, seed=7, curve_id=0), workloads.job(15, 1, seed=8, curve_id=1)]
-    xa = torch.tensor(np.concatenate([rng.standard_normal(1 << 16), np.exp(rng.standard_normal(1 << 15))]),
+    jobs = [workloads.job(16, 1, seed=7, curve_id=0), workloads.job(15, 1, seed=8, curve_id=1),
+            workloads.job(19, 1, seed=9, curve_id=2)]
+    xa = torch.tensor(np.concatenate([rng.standard_normal(1 << 16), np.exp(rng.standard_normal(1 << 15)),
+                                      rng.standard_normal(1 << 19) ** 3]),
                       dtype=torch.float32, device="cuda")
     with Plan(jobs, LC_FP32) as p:
         p.setup()
