@@ -49,8 +49,9 @@ BUCKET_SCATTER_BYTES_PER_ELEMENT = 13 + 16
 SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 = 1.8893e9 / 2 ** 25
 # DRAM bytes (read + write) of one whole iteration per sample of the uniform
 # batch, from one ncu capture of every kernel of an iteration over 512 curves
-# x 2^16 (1.822 GB; the working set exceeds L2 there as at 4096 curves)
-ITER_DRAM_BYTES_PER_SAMPLE = 1822027776 / 2 ** 25
+# x 2^16 with the current kernels (1218.3 MB read + 602.9 MB written; the
+# working set exceeds L2 there as at 4096 curves)
+ITER_DRAM_BYTES_PER_SAMPLE = 1821.2e6 / 2 ** 25
 WORKLOAD = (f"uniform batch: {NCURVES} curves x 2^{LOG2N} samples, dt=1 d, bending PL PSD "
             f"(f_br=1/300 d^-1, slopes 1 and 2), broken-PL ERDF [-4,0] break -1.5 slopes +0.4/-2.5, "
             f"{ITERS} E13 iterations, FP32")
