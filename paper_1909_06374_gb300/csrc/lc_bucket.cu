@@ -111,6 +111,19 @@ int bucket_gmax(uint32_t log2n)
     return 2 * (int)(((size_t)1 << log2n) / (size_t)bucket_cap(log2n)) + 1;
 }
 
+// Finish blocks launched per curve: a little above the 99.9th percentile of
+// the number of groups per curve (measured on a model of the splitter
+// sample: at 2^16 35 groups on average, 36 at most, of gmax = 65 slots; from
+// 2^18 on about 178 of 257), so that few launched blocks find an empty slot.
+// A curve with more groups has them finished by its last launched block.
+int bucket_glaunch(uint32_t log2n)
+{
+    static const int tab[] = {6, 10, 19, 38, 83, 189, 189, 189};  // 2^13 .. 2^20
+    const int i = (int)log2n - 13;
+    const int g = (i >= 0 && i < 8) ? tab[i] : bucket_gmax(log2n);
+    return std::min(g, bucket_gmax(log2n));
+}
+
 size_t bucket_aux_words(uint32_t log2n, int ncurves)
 {
     return (size_t)kAuxHeader + (size_t)ncurves * bucket_curve_words(log2n) +
@@ -149,6 +162,7 @@ struct BkArgs {
     int gmax;
     int cw;                  // aux words per curve
     int cap;                 // finish-group capacity (elements)
+    int glaunch;             // finish blocks launched per curve (<= gmax)
     uint32_t log2n;
 };
 
@@ -713,27 +727,24 @@ struct FinLayout {
 
 // One work-item slot per block (gmax slots per curve); a block whose slot is
 // empty returns at once.
-template <int CAP, bool MULTI>
-__global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
-    k_bk_finish(const __grid_constant__ LaunchSet<BkArgs> set)
+// Ranks the elements of work item `item` (a group of buckets of one curve)
+// and writes x[position] = s[rank]; false when the item is empty.
+template <int CAP>
+__device__ __forceinline__ bool bk_finish_item(const BkArgs& a, uint32_t item, uint32_t* bsm)
 {
     using L = FinLayout<CAP>;
     constexpr int TH = L::THREADS, PER = L::PER;
-    uint32_t blk;
-    const BkArgs& a = set.pick<MULTI>(blk);
     constexpr uint32_t kPosMask = (1u << 24) - 1u;
-    const uint32_t item = blk;
     const uint4 d0 = a.items[2 * item];
     const uint4 d1 = a.items[2 * item + 1];
     const uint32_t e0 = d0.x, b0 = d0.z;
     const int n = (int)d0.y, nb = (int)d0.w;
-    if (n == 0) return;
+    if (n == 0) return false;
     const uint64_t off = (uint64_t)d1.x | ((uint64_t)d1.y << 32);
     const uint32_t* A = a.aux + (size_t)d1.z * a.cw;
-    extern __shared__ __align__(16) uint32_t bsm[];
     if (n > CAP) {  // one bucket of nearly equal values
         bk_oversize<TH>(a, off, e0, n, bsm);
-        return;
+        return true;
     }
     const int ns = kBkSubPer * n;  // sub-buckets of the group
     unsigned long long* kk = (unsigned long long*)(bsm + L::KK);
@@ -861,8 +872,39 @@ __global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
             x[pos[j]] = s[r];
         }
     }
+    return true;
 }
 
+// One block per launched work-item slot: glaunch slots per curve, enough for
+// the groups of almost every curve (a curve's groups fill its first slots, any
+// later slot is empty).
+template <int CAP, bool MULTI>
+__global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
+    k_bk_finish(const __grid_constant__ LaunchSet<BkArgs> set)
+{
+    uint32_t blk;
+    const BkArgs& a = set.pick<MULTI>(blk);
+    extern __shared__ __align__(16) uint32_t bsm[];
+    const uint32_t gl = (uint32_t)a.glaunch;
+    const uint32_t ci = blk / gl, g = blk - ci * gl;
+    bk_finish_item<CAP>(a, ci * (uint32_t)a.gmax + g, bsm);
+}
+
+// The groups of a curve beyond its glaunch launched slots, if any: one block
+// per curve, one group after the other (almost always none).
+template <int CAP, bool MULTI>
+__global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
+    k_bk_finish_tail(const __grid_constant__ LaunchSet<BkArgs> set)
+{
+    uint32_t blk;
+    const BkArgs& a = set.pick<MULTI>(blk);
+    extern __shared__ __align__(16) uint32_t bsm[];
+    const uint32_t gm = (uint32_t)a.gmax;
+    for (uint32_t h = (uint32_t)a.glaunch; h < gm; ++h) {
+        if (!bk_finish_item<CAP>(a, blk * gm + h, bsm)) break;
+        __syncthreads();  // the next group reuses the shared memory
+    }
+}
 
 template <int CAP>
 static cudaError_t finish_attrs()
@@ -871,6 +913,10 @@ static cudaError_t finish_attrs()
     cudaError_t e = cudaFuncSetAttribute(k_bk_finish<CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bk_finish<CAP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bk_finish_tail<CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bk_finish_tail<CAP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -891,14 +937,28 @@ static int launch_sample_sets(const std::vector<BkArgs>& args, const std::vector
     });
 }
 
+// The finish launches of one group capacity, then (for the classes that
+// launch fewer blocks per curve than they have slots) the tail launches.
 template <int CAP>
 static int launch_finish_sets(const std::vector<BkArgs>& args, const std::vector<uint32_t>& blocks, cudaStream_t st)
 {
     using L = FinLayout<CAP>;
-    return for_launch_sets(args, blocks, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+    int n = for_launch_sets(args, blocks, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
         if (multi) k_bk_finish<CAP, true><<<g, L::THREADS, L::SMEM, st>>>(s);
         else k_bk_finish<CAP, false><<<g, L::THREADS, L::SMEM, st>>>(s);
     });
+    std::vector<BkArgs> tail;
+    std::vector<uint32_t> tb;
+    for (size_t i = 0; i < args.size(); ++i) {
+        if (args[i].glaunch >= args[i].gmax) continue;
+        tail.push_back(args[i]);
+        tb.push_back(blocks[i] / (uint32_t)args[i].glaunch);  // one block per curve
+    }
+    n += for_launch_sets(tail, tb, [&](const LaunchSet<BkArgs>& s, uint32_t g, bool multi) {
+        if (multi) k_bk_finish_tail<CAP, true><<<g, L::THREADS, L::SMEM, st>>>(s);
+        else k_bk_finish_tail<CAP, false><<<g, L::THREADS, L::SMEM, st>>>(s);
+    });
+    return n;
 }
 
 template <int TPB>
@@ -946,10 +1006,11 @@ void launch_bucket_argsort(const Plan& p, const std::vector<const ClassInfo*>& k
         a.gmax = bucket_gmax(k.log2n);
         a.cw = bucket_curve_words(k.log2n);
         a.cap = bucket_cap(k.log2n);
+        a.glaunch = bucket_glaunch(k.log2n);
         a.log2n = k.log2n;
         b_curve[i] = (uint32_t)k.ncurves;
         b_tile[i] = (uint32_t)(k.ncurves * a.tpc);
-        b_item[i] = (uint32_t)(k.ncurves * a.gmax);
+        b_item[i] = (uint32_t)(k.ncurves * a.glaunch);
         if (a.tpc >= 2) {
             h2.push_back(a);
             hb2.push_back((uint32_t)(k.ncurves * (a.tpc / 2)));

@@ -90,6 +90,31 @@ def test_results_equal_the_job_alone():
 
 
 @pytest.mark.gpu
+def test_long_jobs_equal_the_job_alone():
+    """Jobs of 2^15..2^20 samples (the sample-sort argsort, with every sample
+    size and finish-group capacity) and shorter ones in the same cohorts: each
+    result equals the job run alone in a plan of its own, bit for bit."""
+    rng = np.random.default_rng(7)
+    lengths = [15, 20, 9, 18, 13, 19, 17, 11, 16, 20]
+    jobs = [workloads.job(n, int(rng.integers(2, 6)), seed=300 + c, curve_id=c,
+                          f_br=float(10 ** rng.uniform(-4, -1)), alpha_high=float(rng.uniform(2, 3)))
+            for c, n in enumerate(lengths)]
+    server = lc_server_create(0, 0, LC_FP32)
+    try:
+        tickets = []
+        for j in jobs:
+            tickets.append(lc_submit(server, j))
+            time.sleep(0.002)
+        out, _ = _drain(server, tickets, jobs)
+    finally:
+        lc_server_destroy(server)
+    for t, j in zip(tickets, jobs):
+        with Plan([j], LC_FP32) as p:
+            alone = p.generate().cpu().numpy()
+        assert np.array_equal(out[t], alone), j["log2n"]
+
+
+@pytest.mark.gpu
 def test_admission_respects_the_budget():
     jobs = [workloads.job(14, 40, seed=c, curve_id=c) for c in range(6)]
     # planes of 2^15 samples: two slots of 2^14
