@@ -891,7 +891,9 @@ __global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
 }
 
 // The groups of a curve beyond its glaunch launched slots, if any: one block
-// per curve, one group after the other (almost always none).
+// per curve, one group after the other (almost always none).  The loop runs
+// to the curve's group count, not to the first empty item: a group of empty
+// buckets (before an oversize bucket) has no elements but later groups do.
 template <int CAP, bool MULTI>
 __global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
     k_bk_finish_tail(const __grid_constant__ LaunchSet<BkArgs> set)
@@ -900,9 +902,9 @@ __global__ void __launch_bounds__(FinLayout<CAP>::THREADS, FinLayout<CAP>::MINB)
     const BkArgs& a = set.pick<MULTI>(blk);
     extern __shared__ __align__(16) uint32_t bsm[];
     const uint32_t gm = (uint32_t)a.gmax;
-    for (uint32_t h = (uint32_t)a.glaunch; h < gm; ++h) {
-        if (!bk_finish_item<CAP>(a, blk * gm + h, bsm)) break;
-        __syncthreads();  // the next group reuses the shared memory
+    const uint32_t ng = min(a.aux[(size_t)blk * a.cw + kAuxGcount], gm);
+    for (uint32_t h = (uint32_t)a.glaunch; h < ng; ++h) {
+        if (bk_finish_item<CAP>(a, blk * gm + h, bsm)) __syncthreads();  // the next group reuses the shared memory
     }
 }
 
