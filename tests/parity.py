@@ -1,6 +1,6 @@
 """Comparison rules between the CUDA path and the FP64 oracle.
 
-Per position (spec acceptance): the GPU's value at position k must be
+Per position (the acceptance rule): the GPU's value at position k must be
 the oracle's, unless the oracle's pre-ranking values (x_adj of the last
 iteration) at the oracle's rank of k and at the rank the GPU's value implies
 differ by less than `tie_rel` times rms(x_adj) (a near tie that FP32 FFT

@@ -1,6 +1,6 @@
 """CUDA path against the FP64 oracle, through the C ABI.
 
-Bars (spec acceptance): ERDF draws and their multiset bit-exact; TK95
+Bars (the acceptance rules): ERDF draws and their multiset bit-exact; TK95
 stage within 2e-5 relative L2; one iteration from the same state equal per
 position except near ties (1e-5 rms of the oracle's pre-ranking series);
 FP64 runs equal end to end except near ties; runs deterministic."""
