@@ -52,6 +52,63 @@ SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 = 1.8893e9 / 2 ** 25
 # x 2^16 with the current kernels (1218.3 MB read + 602.9 MB written; the
 # working set exceeds L2 there as at 4096 curves)
 ITER_DRAM_BYTES_PER_SAMPLE = 1821.2e6 / 2 ** 25
+# Bytes of the sample sort per element (FP32): histogram 4, bucket scatter 4 +
+# 1 + 8, finish 8 + 4 + 4, bucket byte written 1
+BUCKET_SORT_BYTES_PER_ELEMENT = 34
+SAMPLE_SORT_LOG2 = (13, 20)  # FP32 lengths on the sample sort
+FUSED_LOG2 = (10, 14)        # FP32 lengths on the fused on-chip kernels (the built-in path table)
+
+
+def scheduled_bytes_per_sample_iter(jobs, esize, fused_elements):
+    """HBM bytes the scheduled kernels move per sample-iteration (reads +
+    writes at their algorithmic sizes), averaged over the batch's
+    sample-iterations, beside the 14 B floor (28 B in FP64).  Multi-kernel
+    curves: the transforms' passes (tile path, log2 M >= 12: P = ceil(log2 M /
+    9) passes each way, 8 in FP64, the middle two fused into one kernel, so 2P -
+    1 kernels that each read and write the complex array; radix-pass path: P
+    passes each way and the spectral kernel), each 2 esize B per sample, plus
+    the amplitudes (esize / 2 B per sample); then the argsort: the sample
+    sort's 34 B per element, or the radix passes with their histograms
+    (FP32: 4 x 4 + 60 = 76 B; FP64: 8 x 8 + 192 = 256 B).  Fused curves touch
+    HBM once per launch of all iterations: 14 B per sample (FP32) / iterations.
+    Lengths 2^10..2^14 count as fused when their samples equal the plan's fused
+    samples (the built-in path table), none when the plan has none; otherwise
+    the figure is not defined (None).  Without the Eq. 4 pass."""
+    fp32 = esize == 4
+    fused_len = [j for j in jobs if fp32 and FUSED_LOG2[0] <= int(j["log2n"]) <= FUSED_LOG2[1]]
+    fused_n = sum(1 << int(j["log2n"]) for j in fused_len)
+    if fused_elements == 0:
+        fused_ids = set()
+    elif fused_elements == fused_n:
+        fused_ids = {id(j) for j in fused_len}
+    else:
+        return None
+    tot_b, tot_si = 0.0, 0
+    for j in jobs:
+        log2n, iters = int(j["log2n"]), int(j["iters"])
+        n = 1 << log2n
+        if iters <= 0:
+            continue
+        if id(j) in fused_ids:
+            per = ALG_BYTES_PER_SAMPLE_ITER * esize / 4 / iters
+        else:
+            log2m = log2n - 1
+            if log2m >= 12:
+                p = -(-log2m // (9 if fp32 else 8))
+                kernels = 2 * p - 1
+            else:
+                p = (1 if log2m % 4 else 0) + log2m // 4
+                kernels = 2 * p + 1
+            fft = kernels * 2 * esize + esize / 2
+            if fp32 and SAMPLE_SORT_LOG2[0] <= log2n <= SAMPLE_SORT_LOG2[1]:
+                sort = BUCKET_SORT_BYTES_PER_ELEMENT
+            else:
+                passes = esize  # 8-bit digits of esize-byte keys
+                sort = passes * esize + SORT_BYTES_PER_ELEMENT[esize]  # histograms + scatter passes
+            per = fft + sort
+        tot_b += per * n * iters
+        tot_si += n * iters
+    return tot_b / tot_si if tot_si else None
 WORKLOAD = (f"uniform batch: {NCURVES} curves x 2^{LOG2N} samples, dt=1 d, bending PL PSD "
             f"(f_br=1/300 d^-1, slopes 1 and 2), broken-PL ERDF [-4,0] break -1.5 slopes +0.4/-2.5, "
             f"{ITERS} E13 iterations, FP32")
@@ -419,6 +476,8 @@ def gpu_line(args, workload, steps, warmup, dist, e2e_on, cpu_on, extra=False):
                                     "launch_ms": avg_ms, "alg_bytes_per_launch": per_launch_bytes,
                                     "traffic": ktraffic, "alg_bytes_definition": kernel_bytes_def},
                 "group_ms_one_iteration": {g: prof[g] for g in groups},
+                "scheduled_bytes_per_sample_iter": scheduled_bytes_per_sample_iter(jobs, esize,
+                                                                                   prof["fused_elements"]),
                 "setup_ms": setup_ms}
 
         if args.post and not extra:
