@@ -671,14 +671,15 @@ cudaError_t resident_kernel_attributes()
     return e;
 }
 
-// Path table (measured on GB300, 2^28 samples x 200 iterations per length,
-// sample*iter/s): the one-CTA fused kernel wins from 2^10 to 2^14 (2^12:
-// 3.46e10 vs 2.39e10 multi-kernel, 2^13: 3.81e10 vs 2.81e10, 2^14: 3.60e10
-// vs 2.86e10), the multi-kernel path from 2^15 on (2^15: 2.90e10 vs 2.08e10
-// for the 2-CTA cluster kernel; 2^16: 2.90e10, the 4-CTA cluster kernel far
-// behind).  LC_PATH=resident also runs the cluster kernels at 2^15 and 2^16;
-// LC_RESIDENT_MAX_LOG2 moves the crossover of the auto mode (autotune.py
-// measures it on the GPU at hand).
+// Path table of the auto mode: the one-CTA fused kernel from 2^10 to 2^14,
+// the multi-kernel path above.  Set when the multi-kernel path used the LSD
+// argsort (2^14: 3.60e10 fused vs 2.86e10 multi-kernel sample*iter/s on
+// GB300; 2^15: 2.90e10 multi-kernel vs 2.08e10 for the 2-CTA cluster kernel).
+// With the sample sort the multi-kernel path leads from 2^13 on (autotune.py
+// on GB300, 2^26 samples x 20 iterations: 2^12 3.79e10 fused vs 2.51e10,
+// 2^13 4.22e10 vs 4.48e10, 2^14 3.99e10 vs 4.87e10); LC_RESIDENT_MAX_LOG2=12
+// applies that crossover.  LC_PATH=resident also runs the cluster kernels at
+// 2^15 and 2^16.
 bool resident_supported(const Plan& p, uint32_t log2n)
 {
     if (p.prec != LC_FP32 || log2n < kResMinLog2) return false;
