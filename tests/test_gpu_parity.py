@@ -335,11 +335,13 @@ def test_maximum_length_2_27():
         assert not torch.equal(x2, x0)
 
 
-@pytest.mark.parametrize("path,log2n", [("resident", 16), ("resident", 15), ("multi", 12)])
+@pytest.mark.parametrize("path,log2n", [("resident", 16), ("resident", 15), ("multi", 12), ("multi", 13),
+                                        ("multi", 14)])
 def test_forced_paths_one_step(path, log2n, monkeypatch):
     """The per-length table picks one iteration path; every complete path stays
     correct: LC_PATH=resident runs 2^16 curves on the 4-CTA and 2^15 curves on
-    the 2-CTA cluster kernel, LC_PATH=multi runs 2^12 curves on the
+    the 2-CTA cluster kernel, LC_PATH=multi runs 2^12 curves (radix-pass FFT,
+    radix argsort) and 2^13, 2^14 curves (tile FFT, sample sort) on the
     multi-kernel path."""
     monkeypatch.setenv("LC_PATH", path)
     jobs = workloads.uniform(ncurves=3, log2n=log2n, iters=2)
