@@ -34,6 +34,7 @@ constexpr int kResThreads = 512;
 constexpr int kResWarps = kResThreads / 32;
 constexpr uint32_t kResMinLog2 = 10;
 constexpr uint32_t kResMaxLog2 = 14;          // one CTA
+constexpr uint32_t kResAutoMaxLog2 = 12;      // the auto mode's crossover (autotune.py sweep)
 constexpr uint32_t kResClusterMaxLog2 = 16;   // clusters of 2 or 4 CTAs
 constexpr int kTwLo = 128;                    // low twiddle table (W^b, b < 128)
 constexpr int kTwHiMax = 64;                  // high table (W^{128 a}), Mc <= 8192
@@ -671,21 +672,19 @@ cudaError_t resident_kernel_attributes()
     return e;
 }
 
-// Path table of the auto mode: the one-CTA fused kernel from 2^10 to 2^14,
-// the multi-kernel path above.  Set when the multi-kernel path used the LSD
-// argsort (2^14: 3.60e10 fused vs 2.86e10 multi-kernel sample*iter/s on
-// GB300; 2^15: 2.90e10 multi-kernel vs 2.08e10 for the 2-CTA cluster kernel).
-// With the sample sort the multi-kernel path leads from 2^13 on (autotune.py
-// on GB300, 2^26 samples x 20 iterations: 2^12 3.79e10 fused vs 2.51e10,
-// 2^13 4.22e10 vs 4.48e10, 2^14 3.99e10 vs 4.87e10); LC_RESIDENT_MAX_LOG2=12
-// applies that crossover.  LC_PATH=resident also runs the cluster kernels at
-// 2^15 and 2^16.
+// Path table of the auto mode: the one-CTA fused kernel from 2^10 to 2^12,
+// the multi-kernel path above (autotune.py on GB300, 2^26 samples x 20
+// iterations, sample*iter/s fused vs multi-kernel: 2^12 3.79e10 vs 2.51e10,
+// 2^13 4.22e10 vs 4.48e10, 2^14 3.99e10 vs 4.87e10, 2^15 2.20e10 for the
+// 2-CTA cluster kernel vs 4.92e10).  With the LSD argsort the crossover was
+// 2^14.  LC_RESIDENT_MAX_LOG2 (up to 14 for the one-CTA kernel) moves it;
+// LC_PATH=resident also runs the cluster kernels at 2^15 and 2^16.
 bool resident_supported(const Plan& p, uint32_t log2n)
 {
     if (p.prec != LC_FP32 || log2n < kResMinLog2) return false;
     if (p.path_mode == 2) return false;
     if (p.path_mode == 1) return log2n <= kResClusterMaxLog2;
-    return log2n <= (uint32_t)(p.res_max_log2 >= 0 ? p.res_max_log2 : (int)kResMaxLog2);
+    return log2n <= (uint32_t)(p.res_max_log2 >= 0 ? p.res_max_log2 : (int)kResAutoMaxLog2);
 }
 
 size_t resident_exchange_floats(uint32_t log2n)

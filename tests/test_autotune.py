@@ -31,7 +31,7 @@ def test_sweep_runs_both_paths():
 @pytest.mark.parametrize("env,fused", [(None, True), ("9", False), ("12", True), ("11", False)])
 def test_resident_max_log2_moves_the_crossover(env, fused, monkeypatch):
     """A 2^12 curve runs on the fused kernel under the built-in table (crossover
-    2^14) and with LC_RESIDENT_MAX_LOG2 >= 12, on the multi-kernel path below;
+    2^12) and with LC_RESIDENT_MAX_LOG2 >= 12, on the multi-kernel path below;
     the one-iteration profile shows which kernels ran."""
     torch = pytest.importorskip("torch")
     from paper_1909_06374_gb300 import LC_FP32, Plan, lc_plan_profile, workloads
