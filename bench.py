@@ -56,7 +56,7 @@ ITER_DRAM_BYTES_PER_SAMPLE = 1821.2e6 / 2 ** 25
 # 1 + 8, finish 8 + 4 + 4, bucket byte written 1
 BUCKET_SORT_BYTES_PER_ELEMENT = 34
 SAMPLE_SORT_LOG2 = (13, 20)  # FP32 lengths on the sample sort
-FUSED_LOG2 = (10, 14)        # FP32 lengths on the fused on-chip kernels (the built-in path table)
+FUSED_LOG2 = (10, 14)        # FP32 lengths the one-CTA fused kernel can take
 
 
 def scheduled_bytes_per_sample_iter(jobs, esize, fused_elements):
@@ -71,17 +71,18 @@ def scheduled_bytes_per_sample_iter(jobs, esize, fused_elements):
     sort's 34 B per element, or the radix passes with their histograms
     (FP32: 4 x 4 + 60 = 76 B; FP64: 8 x 8 + 192 = 256 B).  Fused curves touch
     HBM once per launch of all iterations: 14 B per sample (FP32) / iterations.
-    Lengths 2^10..2^14 count as fused when their samples equal the plan's fused
-    samples (the built-in path table), none when the plan has none; otherwise
-    the figure is not defined (None).  Without the Eq. 4 pass."""
+    The fused curves are those of 2^10..2^top for the top length whose
+    samples add up to the plan's fused samples (the path table's crossover,
+    2^12 built in, or LC_RESIDENT_MAX_LOG2); with no such top the figure is
+    not defined (None).  Without the Eq. 4 pass."""
     fp32 = esize == 4
-    fused_len = [j for j in jobs if fp32 and FUSED_LOG2[0] <= int(j["log2n"]) <= FUSED_LOG2[1]]
-    fused_n = sum(1 << int(j["log2n"]) for j in fused_len)
-    if fused_elements == 0:
-        fused_ids = set()
-    elif fused_elements == fused_n:
-        fused_ids = {id(j) for j in fused_len}
-    else:
+    fused_ids = None
+    for top in range(FUSED_LOG2[0] - 1, FUSED_LOG2[1] + 1):
+        fused_len = [j for j in jobs if fp32 and FUSED_LOG2[0] <= int(j["log2n"]) <= top]
+        if sum(1 << int(j["log2n"]) for j in fused_len) == fused_elements:
+            fused_ids = {id(j) for j in fused_len}
+            break
+    if fused_ids is None:
         return None
     tot_b, tot_si = 0.0, 0
     for j in jobs:

@@ -44,8 +44,8 @@ def test_scheduled_bytes_per_sample_iteration():
     34 B) 60 B; the long curves (2^26: five FFT kernels, radix argsort 76 B)
     118 B; the FP64 single curve (2^14: three FFT kernels of 16 B + 4 B, 256 B
     of radix passes) 308 B; the ragged batch between its fused and its
-    multi-kernel curves' figures, undefined when the fused samples do not
-    match the built-in path table."""
+    multi-kernel curves' figures, undefined when the fused samples match no
+    crossover of the path table."""
     import bench
     jobs, _, _, _ = bench.rank_jobs("uniform", 0, 1)
     assert bench.scheduled_bytes_per_sample_iter(jobs, 4, 0) == 60.0
@@ -54,7 +54,8 @@ def test_scheduled_bytes_per_sample_iteration():
     jobs, _, _, _ = bench.rank_jobs("single", 0, 1)
     assert bench.scheduled_bytes_per_sample_iter(jobs, 8, 0) == 308.0
     jobs, _, _, _ = bench.rank_jobs("ragged", 0, 1)
-    fused = sum(1 << j["log2n"] for j in jobs if 10 <= j["log2n"] <= 14)
-    v = bench.scheduled_bytes_per_sample_iter(jobs, 4, fused)
-    assert 14.0 / 100 < v < 118.0
+    for top in (12, 14):  # the built-in crossover and LC_RESIDENT_MAX_LOG2=14
+        fused = sum(1 << j["log2n"] for j in jobs if 10 <= j["log2n"] <= top)
+        v = bench.scheduled_bytes_per_sample_iter(jobs, 4, fused)
+        assert 14.0 / 100 < v < 118.0
     assert bench.scheduled_bytes_per_sample_iter(jobs, 4, fused + 1) is None
