@@ -192,7 +192,7 @@ LC_API lc_status lc_set_state(lc_plan plan, const void* in_x, void* stream);
  * s_c are the curve's sorted draws and perm_c the stable ascending argsort of
  * x_adj's curve c (ties, -0 = +0 included, keep the lower position first).
  * The plan's own sort path runs (the sample sort of FP32 curves of 2^13 ..
- * 2^17 samples, else the LSD radix passes).
+ * 2^20 samples, else the LSD radix passes).
  *   x_adj: device pointer, sum_c N_c elements in the plan's precision and
  *          layout (curve c at the offset of lc_get_state); read only; values
  *          must not be NaN.

@@ -2,13 +2,13 @@
 
 Two complete iteration paths exist for FP32 curves of 2^10..2^16 samples: the
 fused on-chip kernels (one CTA per curve up to 2^14, clusters of 2 and 4 CTAs
-at 2^15 and 2^16) and the multi-kernel path (tile FFT passes + radix sort
-passes through HBM).  Which is faster depends on the length and on the GPU.
+at 2^15 and 2^16) and the multi-kernel path (tile FFT passes + the sample-sort
+or radix argsort through HBM).  Which is faster depends on the length and on the GPU.
 For every length in the range this sweep runs a uniform batch of about
 2^samples samples for `iters` iterations on each path, timed with CUDA events
 around the iteration stage (lc_plan_timing), and reports the crossover: the
 longest length up to which the fused kernels win at every length.  The
-library's auto mode uses the crossover measured on GB300 (2^14); the
+library's auto mode uses the crossover measured on GB300 (2^12); the
 environment variable LC_RESIDENT_MAX_LOG2 applies another one (read when a
 plan is created).  Results depend on the length, the precision and the path,
 so a different crossover changes the bits of the affected lengths (both paths
