@@ -32,10 +32,13 @@
 //                 one are placed side by side and ranked among themselves by
 //                 (value, position) -- the stable argsort order, whatever
 //                 order the scatter left.  rank = group base + rank in the
-//                 group; the block writes x[position] = s[rank].
+//                 group; the block writes x[position] = s[rank].  Blocks
+//                 are launched for the first glaunch slots of each curve;
+//   k_bk_finish_tail one block per curve for any groups beyond them.
 // A bucket of more than CAP elements (a spike of equal or nearly equal
-// values, or rarely a wide bucket) is one group of its own, sorted by a block-level LSD radix sort on
-// (value, position) through global memory instead.
+// values, or rarely a wide bucket) is one group of its own, sorted by a
+// block-level LSD radix sort on (value, position) through global memory
+// instead.
 //
 // HBM bytes per element: 4 (histogram) + 4 + 1 + 8 (scatter, incl. the
 // bucket byte) + 8 + 4 + 4 (finish) + 1 (bucket byte written) = 34, against
@@ -115,7 +118,7 @@ int bucket_gmax(uint32_t log2n)
 // the number of groups per curve (measured on a model of the splitter
 // sample: at 2^16 35 groups on average, 36 at most, of gmax = 65 slots; from
 // 2^18 on about 178 of 257), so that few launched blocks find an empty slot.
-// A curve with more groups has them finished by its last launched block.
+// A curve with more groups has the rest finished by k_bk_finish_tail.
 int bucket_glaunch(uint32_t log2n)
 {
     static const int tab[] = {6, 10, 19, 38, 83, 189, 189, 189};  // 2^13 .. 2^20
