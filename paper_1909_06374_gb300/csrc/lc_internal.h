@@ -13,8 +13,8 @@
 
 namespace lc {
 
-// Curves of one length N = 2^log2n; every launch of the multi-kernel path
-// covers one class.
+// Curves of one length N = 2^log2n; a launch of the multi-kernel path covers
+// one class or, through a LaunchSet, several classes of one stage.
 struct ClassInfo {
     uint32_t log2n = 0;
     int ncurves = 0;
