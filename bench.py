@@ -49,9 +49,12 @@ BUCKET_SCATTER_BYTES_PER_ELEMENT = 13 + 16
 SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 = 1.8893e9 / 2 ** 25
 # DRAM bytes (read + write) of one whole iteration per sample of the uniform
 # batch, from one ncu capture of every kernel of an iteration over 512 curves
-# x 2^16 with the current kernels (1218.3 MB read + 602.9 MB written; the
-# working set exceeds L2 there as at 4096 curves)
+# x 2^16 (1218.3 MB read + 602.9 MB written; the working set exceeds L2 there
+# as at 4096 curves).  The finish kernel's launch shape has changed since
+# (fewer empty blocks, a tail launch), so the bench line reports it as the
+# last capture's figure and leaves `traffic` null.
 ITER_DRAM_BYTES_PER_SAMPLE = 1821.2e6 / 2 ** 25
+ITER_DRAM_CAPTURE_CURRENT = False
 # Bytes of the sample sort per element (FP32): histogram 4, bucket scatter 4 +
 # 1 + 8, finish 8 + 4 + 4, bucket byte written 1
 BUCKET_SORT_BYTES_PER_ELEMENT = 34
@@ -460,16 +463,20 @@ def gpu_line(args, workload, steps, warmup, dist, e2e_on, cpu_on, extra=False):
         ktraffic = None
         if dominant == "sort_scatter" and esize == 4 and not prof.get("bucket_elements", 0):
             ktraffic = SCATTER_DRAM_BYTES_PER_ELEMENT_FP32 * prof["sorted_elements"] / launches_k
-        traffic = None
+        traffic, last_capture = None, None
         if workload == "uniform" and (args.curves, args.log2n) == (NCURVES, LOG2N) and ITER_DRAM_BYTES_PER_SAMPLE:
-            traffic = ITER_DRAM_BYTES_PER_SAMPLE * samples
+            if ITER_DRAM_CAPTURE_CURRENT:
+                traffic = ITER_DRAM_BYTES_PER_SAMPLE * samples
+            last_capture = {"dram_bytes_per_sample_iter": ITER_DRAM_BYTES_PER_SAMPLE,
+                            "of": "every kernel of one iteration, 512 curves x 2^16, before the finish kernel's "
+                                  "launched-slot change"}
         # The roofline unit is one amplitude-adjustment iteration of every curve
         # (one replay of the iteration graph): 14 B per sample-iteration (28 B in
         # FP64) over the iteration stage's CUDA-event time.  The dominant kernel's
         # figure against its own algorithmic bytes is kept beside it.
         n_iter = max(1, max(int(j["iters"]) for j in jobs))
         roof = {"bound": "hbm", "achieved": stage_gbs, "peak": peak, "unit": "GB/s", "frac": stage_gbs / peak,
-                "traffic": traffic,
+                "traffic": traffic, "traffic_last_capture": last_capture,
                 "kernel": "iteration stage: every kernel of one E13 iteration of every curve (one graph replay)",
                 "alg_bytes_per_sample_iter": alg_per, "alg_bytes_per_launch": alg_per * sample_iters / n_iter,
                 "launch_ms": it_ms / n_iter, "iterate_ms": it_ms, "peak_kind": peak_kind,
